@@ -1,0 +1,158 @@
+/*
+ * msg_mimc.h -- C ABI of the GB300 MSG-MIMC hot path (arXiv:1907.12334).
+ *
+ * One sample of the method is: draw xi ~ N(0,1), form the Gaussian field
+ * Z = Phi diag(sqrt(lambda)) xi, set a = exp(Z), solve -div(a grad u) = 1 on
+ * [0,1]^2 (u = 0 on the boundary, Sec. 1 Eq. (1.1)) by Full Multiple
+ * Semi-Coarsened multigrid (Sec. 2, Algorithms 1 and 2) on every grid
+ * G^(p,q), 1 <= p <= P, 1 <= q <= Q, of the semi-coarsened hierarchy
+ * (Eq. (2.1)), take the quantity of interest on each grid (Sec. 4) and form
+ * the multi-index differences (Sec. 3, Eq. (3.2)) and the estimator term Y
+ * (Eq. (3.6)).
+ *
+ * Conventions for every entry point:
+ *   - pointers marked [device] are device memory owned by the caller (for
+ *     example allocated through PyTorch); the library never allocates them,
+ *     never frees them and keeps no reference after the call returns;
+ *   - pointers marked [host] are host memory read during the call only;
+ *   - work is enqueued on `stream` (a cudaStream_t passed as void*, NULL for
+ *     the legacy default stream); results are valid once the stream is
+ *     synchronised.  msg_solve_batch additionally synchronises `stream` while
+ *     it runs (it reads per-step convergence counts on the host);
+ *   - the return value is MSG_OK or an error code; on error
+ *     msg_last_error() returns a description (thread-local string);
+ *   - no entry point traps or aborts; per-sample numerical failures are
+ *     reported in the per-sample status words.
+ */
+#ifndef MSG_MIMC_H
+#define MSG_MIMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MSG_OK 0
+#define MSG_ERR_INVALID 1     /* bad argument (size, shape, null pointer, parameter) */
+#define MSG_ERR_WORKSPACE 2   /* workspace smaller than msg_workspace_bytes() */
+#define MSG_ERR_CUDA 3        /* a CUDA runtime call failed */
+#define MSG_ERR_UNSUPPORTED 4 /* option not built or not supported on this device */
+
+/* per-sample status bits written by msg_solve_batch */
+#define MSG_SAMPLE_NOT_CONVERGED 1 /* some grid hit max_cycles before eps */
+#define MSG_SAMPLE_NONFINITE 2     /* a residual norm became NaN or Inf */
+
+/* arithmetic of the inner multigrid cycles */
+#define MSG_PREC_FP64 0  /* every step in FP64 */
+#define MSG_PREC_MIXED 1 /* cycles in FP32; outer residual, update, interpolation, QoI in FP64 */
+
+/* quantity of interest (Sec. 4) */
+#define MSG_QOI_INTEGRAL 0 /* integral of u over D, trapezoid rule */
+#define MSG_QOI_POINT 1    /* Q1 = u(1/2,1/2) */
+#define MSG_QOI_SUBDOMAIN 2 /* Q2 = mean of u over [1/4,1/2]^2, 2-D trapezoid (NaN if p<2 or q<2) */
+#define MSG_QOI_FLUX 3     /* Q3 = -int_0^1 a(1,y) du/dx(1,y) dy, trapezoid + one-sided difference */
+
+/* KL contraction arithmetic */
+#define MSG_GEMM_FP64 0  /* FP64 products and sums */
+#define MSG_GEMM_BF16X3 1 /* tensor cores: bf16 hi/lo splits, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+#define MSG_GEMM_FP32 2  /* FP32 products and sums (SIMT) */
+
+/* Solver parameters (Sec. 2 and its numerical setup: W(2,2) cycles, mu = 2,
+ * red-black Gauss-Seidel, damping omega of the coarse-grid correction,
+ * adaptive nu_0 until ||r||/||b|| <= eps on each grid). */
+typedef struct {
+    int32_t mu;         /* 1 = V-cycle, 2 = W-cycle */
+    int32_t nu1, nu2;   /* pre- and post-smoothing sweeps */
+    int32_t max_cycles; /* cap on cycles per grid */
+    double eps;         /* relative residual target per grid */
+    double omega;       /* damping of the coarse-grid correction */
+    int32_t precision;  /* MSG_PREC_* */
+    int32_t qoi;        /* MSG_QOI_* */
+} msg_params;
+
+/* ------------------------------------------------------------------------ */
+/* (a1) xi: standard normals from Philox4x64-10 (Salmon et al., SC'11) and  */
+/* Box-Muller.  Not in the paper (which samples by circulant embedding); the  */
+/* KL sampler needs i.i.d. N(0,1) coefficients.                              */
+/*                                                                          */
+/* xi[i*M + m] for 0 <= i < S, 0 <= m < M is normal number m of global       */
+/* sample s0 + i: block j = m/4 uses counter (j, s0+i, 0, 0), key (seed, 0); */
+/* word w -> U = (w >> 11) 2^-53; (U0,U1) and (U2,U3) give                    */
+/* sqrt(-2 ln(1-Ua)) * (cos, sin)(2 pi Ub).                                  */
+/*   xi [device] double [S][M], written.  S >= 0, 1 <= M.                    */
+int32_t msg_normals(uint64_t seed, uint64_t s0, int64_t S, int32_t M, double* xi, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a2) Truncated KL field Z = Phi diag(sqrt(lambda)) xi for S samples.     */
+/* Phi [npts][M] and sqrt(lambda) [M] describe the field law on the field    */
+/* grid of one shape (nodes of G^(P+1,Q+1), point index Fy*NFx + Fx).         */
+/*                                                                          */
+/* kl_prepare converts the FP64 basis once into the layout `mode` uses:      */
+/*   Phi, sqrt_lambda [device] double, read.                                 */
+/*   prepared [device] bytes >= kl_prepared_bytes(npts, M, mode), written.   */
+/* sample_field contracts it with xi:                                       */
+/*   xi [device] double [S][M], read.                                        */
+/*   Z  [device] double [S][npts] (or float if z_fp32 != 0), written.         */
+size_t kl_prepared_bytes(int64_t npts, int32_t M, int32_t mode);
+int32_t kl_prepare(const double* Phi, const double* sqrt_lambda, int64_t npts, int32_t M, int32_t mode,
+                   void* prepared, size_t prepared_bytes, void* stream);
+int32_t sample_field(const void* prepared, int64_t npts, int32_t M, int32_t mode, const double* xi,
+                     int64_t S, void* Z, int32_t z_fp32, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a3)-(a13) Batched FMSG solve.                                            */
+/*                                                                          */
+/* Sample i has finest grid (P_i, Q_i) = (PQ[2i], PQ[2i+1]), 1 <= P_i, Q_i    */
+/* <= 12, and its field on the (2^(P_i+1)+1) x (2^(Q_i+1)+1) nodes of        */
+/* G^(P_i+1,Q_i+1), x fastest; fields are packed back to back in sample      */
+/* order.  a = exp(Z) is taken at each grid's face midpoints (x-face         */
+/* (i+1/2, j) of G^(p,q) at field node ((2i+1)2^(P-p), 2j 2^(Q-q)), y-face    */
+/* at (2i 2^(P-p), (2j+1)2^(Q-q))).  The right-hand side is h = 1.           */
+/*                                                                          */
+/* Every grid (p,q) of the sample is solved to ||1 - A u||/||1|| <= eps:      */
+/* diagonals p+q are processed in increasing order (Algorithm 2); a grid     */
+/* starts from the kappa-weighted cubic interpolation of its children's      */
+/* solutions and is iterated by mu-cycles of Algorithm 1 over its own        */
+/* hierarchy {(p',q'): p' <= p, q' <= q}.                                    */
+/*                                                                          */
+/*   PQ      [host]   int32 [S][2].                                          */
+/*   Z       [device] double, sum_i (2^(P_i+1)+1)(2^(Q_i+1)+1) values, read. */
+/*   Qout    [device] double, sum_i P_i Q_i values, written: QoI of grid      */
+/*           (p,q) of sample i at offset_i + (p-1) Q_i + (q-1).              */
+/*   status  [device] int32 [S], written (MSG_SAMPLE_* bits); may be NULL.    */
+/*   cycles  [device] int32, packed like Qout: cycles used per grid; may be NULL. */
+/*   relres  [device] double, packed like Qout: final ||r||/||b||; may be NULL. */
+/*   workspace [device], ws_bytes >= msg_workspace_bytes(PQ, S, prm).       */
+size_t msg_workspace_bytes(const int32_t* PQ, int64_t S, const msg_params* prm);
+int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, const double* Z, double* Qout,
+                        int32_t* status, int32_t* cycles, double* relres, void* workspace, size_t ws_bytes,
+                        void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a14) Multi-index differences (Sec. 3, Eq. (3.2)) and Y (Eq. (3.6)).       */
+/*                                                                          */
+/* Sample i has multi-index L_i = (L[2i], L[2i+1]) >= 0 and grid QoIs packed  */
+/* as msg_solve_batch writes them for finest grid (p0 + L_i1, q0 + L_i2), so */
+/* Q_l = QoI of grid (p0 + l1, q0 + l2).  For 0 <= tau <= L_i:               */
+/*   dQ_tau = D_2 D_1 Q_tau, D_j Q_l = Q_l - Q_{l-e_j} if l_j > 0 else Q_l,   */
+/* packed per sample row-major [L_i1+1][L_i2+1], samples back to back.        */
+/* If ptau != NULL (host, row-major [ld1][ld2], p_tau = P(L >= tau)), also    */
+/* Y_i = sum_tau dQ_tau / p_tau.                                              */
+/*   L [host] int32 [S][2]; Q [device] double, read; dQ [device] double,      */
+/*   written; ptau [host] double or NULL; Y [device] double [S] or NULL.       */
+int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
+                         const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream);
+
+/* Description of the last error on this thread ("" if none). */
+const char* msg_last_error(void);
+
+/* Library version string. */
+const char* msg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSG_MIMC_H */

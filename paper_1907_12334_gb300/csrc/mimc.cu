@@ -1,0 +1,88 @@
+// mimc.cu -- multi-index differences (Sec. 3, Eq. (3.2)) and the per-sample
+// estimator term Y (Eq. (3.6)).  Index arithmetic is integer; the differences
+// are formed in the order D_1 then D_2 of the worked example of Sec. 3.
+#include <vector>
+
+#include "common.cuh"
+
+namespace msg {
+
+struct MimcSample {
+    int L1, L2;
+    int64_t q_off;   // start of the sample's QoIs (finest grid (p0+L1, q0+L2))
+    int64_t d_off;   // start of the sample's (L1+1)(L2+1) differences
+};
+
+__global__ void k_mimc(const MimcSample* smp, int64_t S, int p0, int q0, const double* Q, const double* ptau, int ld2,
+                       double* dQ, double* Y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
+        const MimcSample m = smp[i];
+        const int Qn = q0 + m.L2;  // columns of the sample's QoI block
+        const double* Qs = Q + m.q_off;
+        double y = 0.0;
+        for (int t1 = 0; t1 <= m.L1; ++t1)
+            for (int t2 = 0; t2 <= m.L2; ++t2) {
+                double d1 = Qs[(p0 + t1 - 1) * Qn + (q0 + t2 - 1)];
+                if (t1 > 0) d1 -= Qs[(p0 + t1 - 2) * Qn + (q0 + t2 - 1)];
+                double d = d1;
+                if (t2 > 0) {
+                    double d1m = Qs[(p0 + t1 - 1) * Qn + (q0 + t2 - 2)];
+                    if (t1 > 0) d1m -= Qs[(p0 + t1 - 2) * Qn + (q0 + t2 - 2)];
+                    d = d1 - d1m;
+                }
+                dQ[m.d_off + t1 * (m.L2 + 1) + t2] = d;
+                if (ptau) y += d / ptau[t1 * ld2 + t2];
+            }
+        if (Y) Y[i] = ptau ? y : 0.0;
+    }
+}
+
+}  // namespace msg
+
+using namespace msg;
+
+extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
+                                    const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream)
+{
+    clear_error();
+    if (S < 0 || p0 < 1 || q0 < 1) { set_error("mimc_differences: need S >= 0, p0 >= 1, q0 >= 1"); return MSG_ERR_INVALID; }
+    if (S == 0) return MSG_OK;
+    if (!L || !Q || !dQ) { set_error("mimc_differences: NULL pointer"); return MSG_ERR_INVALID; }
+    std::vector<MimcSample> h(S);
+    int64_t qo = 0, dof = 0;
+    int maxL1 = 0, maxL2 = 0;
+    for (int64_t i = 0; i < S; ++i) {
+        int l1 = L[2 * i], l2 = L[2 * i + 1];
+        if (l1 < 0 || l2 < 0 || p0 + l1 > 12 || q0 + l2 > 12) {
+            set_error("mimc_differences: multi-index out of range");
+            return MSG_ERR_INVALID;
+        }
+        h[i] = MimcSample{l1, l2, qo, dof};
+        qo += (int64_t)(p0 + l1) * (q0 + l2);
+        dof += (int64_t)(l1 + 1) * (l2 + 1);
+        maxL1 = l1 > maxL1 ? l1 : maxL1;
+        maxL2 = l2 > maxL2 ? l2 : maxL2;
+    }
+    if (ptau && (ld1 <= maxL1 || ld2 <= maxL2)) {
+        set_error("mimc_differences: ptau table smaller than the largest multi-index");
+        return MSG_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // tables go through one temporary device block released after the stream drains
+    size_t tb = sizeof(MimcSample) * S, pb = ptau ? sizeof(double) * ld1 * ld2 : 0;
+    char* dbuf = nullptr;
+    MSG_CUDA_TRY(cudaMallocAsync((void**)&dbuf, tb + pb + 256, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(dbuf, h.data(), tb, cudaMemcpyHostToDevice, st));
+    double* dp = nullptr;
+    if (ptau) {
+        dp = (double*)(dbuf + (tb + 255) / 256 * 256);
+        MSG_CUDA_TRY(cudaMemcpyAsync(dp, ptau, pb, cudaMemcpyHostToDevice, st));
+    }
+    int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
+    k_mimc<<<blocks, 256, 0, st>>>((const MimcSample*)dbuf, S, p0, q0, Q, dp, ld2, dQ, Y);
+    MSG_CHECK_LAUNCH();
+    MSG_CUDA_TRY(cudaFreeAsync(dbuf, st));
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host tables above must outlive the copies
+    return MSG_OK;
+}

@@ -1,0 +1,997 @@
+// solver.cu -- batched FMSG solve (Sec. 2, Algorithms 1 and 2 of arXiv:1907.12334).
+//
+// Work decomposition.  Every grid (p,q) of every sample is an *item*: it is
+// solved at stage L = (p-1)+(q-1) (the diagonals are processed in increasing
+// order, Algorithm 2).  An item starts from the kappa-weighted cubic
+// interpolation of its children's solutions and is iterated by mu-cycles of
+// Algorithm 1 over its own hierarchy {(p',q'): p' <= p, q' <= q} until
+// ||1 - A u||/||1|| <= eps.  Each cycle is a defect correction: the FP64
+// residual r = 1 - A u is formed on the item's grid, one mu-cycle of
+// Algorithm 1 (in FP32 for MSG_PREC_MIXED, FP64 otherwise) solves A e = r
+// approximately from e = 0 on the item's scratch hierarchy, and u += e in FP64.
+// For a linear cycle this is the same iteration as cycling on (u, 1).
+//
+// Launch structure of one cycle for all active items of a stage: diagonals
+// d > dcut of the items' hierarchies are visited by one launch per visit half
+// (PRE: zero/smooth nu1/restrict; POST: prolong/smooth nu2) with one CTA per
+// (item, grid) task; everything at or below dcut runs inside one launch
+// (LOW) with one CTA per item walking the recursion of Algorithm 1.
+//
+// Storage (all node-indexed with the boundary, see common.cuh):
+//   u64          solution of every grid of every sample (FP64)
+//   ax64, ay64   a/dx^2 at x-faces (i+1/2,j) and a/dy^2 at y-faces (i,j+1/2),
+//                stored at node (i,j) (FP64; exact scaling by powers of two)
+//   ax32, ay32   the same rounded to FP32 (mixed cycles only)
+//   su, sbx, sby scratch of the active items' hierarchies: correction e and the
+//                restrictions received from the x-parent and the y-parent.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace msg {
+
+// ---------------------------------------------------------------- tables --
+
+struct SampleInfo {
+    int P, Q;
+    int64_t node_off;  // start of the sample's rectangle in u64 / coefficient arrays
+    int64_t field_off; // start of the sample's field in Z
+    int64_t q_off;     // start of the sample's P*Q outputs
+};
+
+// One launch covers a list of segments; segment i owns blocks
+// [blk_start[i], blk_start[i] + count of its group) and each of those blocks
+// is one sample of the group.
+struct Segment {
+    int g;          // shape group
+    int pi, qi;     // item (top) grid
+    int p, q;       // task grid (equal to the item grid for item-level lists)
+    int64_t blk_start;
+    int64_t scr_slot; // offset of the item's hierarchy inside the sample's stage scratch
+};
+
+struct Group {
+    int P, Q;
+    int start, count;  // range in perm[]
+    int64_t scr_start; // start of the group's stage scratch (per stage, set when the stage runs)
+    int64_t scr_per_sample;
+};
+
+struct DevCtx {
+    const SampleInfo* samples;
+    const int* perm;
+    const Group* groups;
+    const Segment* segs;
+    int nseg;
+};
+
+__device__ __forceinline__ int find_segment(const Segment* segs, int nseg, int64_t b)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].blk_start <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct TaskRef {
+    int s;          // sample
+    const Segment* seg;
+    int64_t scr;    // item hierarchy scratch base
+    int64_t item;   // global item id (packed like Qout)
+};
+
+__device__ __forceinline__ TaskRef resolve(const DevCtx& cx)
+{
+    int64_t b = blockIdx.x;
+    int si = find_segment(cx.segs, cx.nseg, b);
+    const Segment* sg = &cx.segs[si];
+    const Group& G = cx.groups[sg->g];
+    int local = (int)(b - sg->blk_start);
+    TaskRef t;
+    t.s = cx.perm[G.start + local];
+    t.seg = sg;
+    t.scr = G.scr_start + (int64_t)local * G.scr_per_sample + sg->scr_slot;
+    const SampleInfo& S = cx.samples[t.s];
+    t.item = S.q_off + (int64_t)(sg->pi - 1) * S.Q + (sg->qi - 1);
+    return t;
+}
+
+// ------------------------------------------------------------ grid ops ----
+
+template <class T>
+struct GView {
+    T* u;
+    const T* bx;
+    const T* by;
+    int bmode;  // 0: b = bx, 1: b = by, 2: b = bx/2 + by/2
+    const T* ax;
+    const T* ay;
+    int nx, ny;
+};
+
+template <class T>
+__device__ __forceinline__ T b_at(const GView<T>& g, int c)
+{
+    if (g.bmode == 0) return g.bx[c];
+    if (g.bmode == 1) return g.by[c];
+    return T(0.5) * g.bx[c] + T(0.5) * g.by[c];
+}
+
+template <class T>
+__device__ __forceinline__ T res_at(const GView<T>& g, int c, int W)
+{
+    T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
+    T Au = (aw + ae + as + an) * g.u[c] - (aw * g.u[c - 1] + ae * g.u[c + 1]) - (as * g.u[c - W] + an * g.u[c + W]);
+    return b_at(g, c) - Au;
+}
+
+// CTA-wide: zero u on every node, boundary included.  Scratch is reused by
+// hierarchies of other shapes from stage to stage, so a boundary node here may
+// hold an interior value written by an earlier stage.
+template <class T>
+__device__ void cta_zero(const GView<T>& g)
+{
+    const int n = (g.nx + 1) * (g.ny + 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) g.u[k] = T(0);
+}
+
+// CTA-wide red-black Gauss-Seidel sweeps (red = (i+j) even first).
+template <class T>
+__device__ void cta_smooth(const GView<T>& g, int sweeps)
+{
+    const int W = g.nx + 1, half = g.nx >> 1, n = (g.ny - 1) * half;
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                int j = 1 + k / half, kk = k % half;
+                int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
+                if (i >= g.nx) continue;
+                int c = j * W + i;
+                T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
+                T nb = (aw * g.u[c - 1] + ae * g.u[c + 1]) + (as * g.u[c - W] + an * g.u[c + W]);
+                g.u[c] = (b_at(g, c) + nb) / (aw + ae + as + an);
+            }
+            __syncthreads();
+        }
+}
+
+// Coarsest grid (1,1): one unknown, v = b / A (Algorithm 1, L = 0).
+template <class T>
+__device__ void cta_coarsest(const GView<T>& g)
+{
+    if (threadIdx.x < 9) {  // all 3x3 nodes: boundary zeros (see cta_zero) and the unknown
+        const int c = 1 * 3 + 1;
+        g.u[threadIdx.x] = (threadIdx.x == c) ? b_at(g, c) / (g.ax[c - 1] + g.ax[c] + g.ay[c - 3] + g.ay[c]) : T(0);
+    }
+    __syncthreads();
+}
+
+// Full-weighting restriction of the residual of g (Eq. (2.3)): R_x r into the
+// x-child's bx (if cxb != nullptr), R_y r into the y-child's by.
+template <class T>
+__device__ void cta_restrict(const GView<T>& g, T* cxb, T* cyb)
+{
+    const int W = g.nx + 1;
+    if (cxb) {  // child (p-1,q): nx/2 cells, same rows
+        const int ncx = g.nx >> 1, Wc = ncx + 1, n = (ncx - 1) * (g.ny - 1);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int ic = 1 + k % (ncx - 1), j = 1 + k / (ncx - 1);
+            int c = j * W + 2 * ic;
+            T v = T(0.25) * (res_at(g, c - 1, W) + T(2) * res_at(g, c, W) + res_at(g, c + 1, W));
+            cxb[j * Wc + ic] = v;
+        }
+    }
+    if (cyb) {  // child (p,q-1): same columns, ny/2 cells
+        const int ncy = g.ny >> 1, n = (g.nx - 1) * (ncy - 1);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int i = 1 + k % (g.nx - 1), jc = 1 + k / (g.nx - 1);
+            int c = 2 * jc * W + i;
+            T v = T(0.25) * (res_at(g, c - W, W) + T(2) * res_at(g, c, W) + res_at(g, c + W, W));
+            cyb[jc * W + i] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// Coarse-grid correction (Eq. (2.4) with linear P and the weights of Eq. (2.5)):
+// u += omega * (kx Px e_x + ky Py e_y); one child only when q = 1 or p = 1.
+template <class T>
+__device__ void cta_prolong(const GView<T>& g, const T* ucx, const T* ucy, T omega)
+{
+    const int W = g.nx + 1, n = (g.nx - 1) * (g.ny - 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = 1 + k % (g.nx - 1), j = 1 + k / (g.nx - 1);
+        int c = j * W + i;
+        T vx = T(0), vy = T(0);
+        if (ucx) {
+            const int Wc = (g.nx >> 1) + 1, r = j * Wc + (i >> 1);
+            vx = (i & 1) ? T(0.5) * (ucx[r] + ucx[r + 1]) : ucx[r];
+        }
+        if (ucy) {
+            const int r = (j >> 1) * W + i;
+            vy = (j & 1) ? T(0.5) * (ucy[r] + ucy[r + W]) : ucy[r];
+        }
+        T corr;
+        if (ucx && ucy) {
+            T cxv = g.ax[c - 1] + g.ax[c], cyv = g.ay[c - W] + g.ay[c];
+            T x2 = cxv * cxv, y2 = cyv * cyv;
+            corr = (x2 / (x2 + y2)) * vx + (y2 / (x2 + y2)) * vy;
+        } else {
+            corr = ucx ? vx : vy;
+        }
+        g.u[c] += omega * corr;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------- hierarchy views --
+
+template <class T>
+struct Hier {
+    T* su;
+    T* sbx;
+    T* sby;
+    const T* ax;  // sample's coefficient rectangle
+    const T* ay;
+    int Ps, Qs;   // sample's finest grid (coefficient layout)
+    int pi, qi;   // item's top grid (scratch layout)
+    int64_t scr;  // item scratch base
+};
+
+template <class T>
+__device__ __forceinline__ GView<T> view_of(const Hier<T>& h, int p, int q)
+{
+    GView<T> g;
+    int64_t so = h.scr + grid_offset(p, q, h.qi);
+    int64_t co = grid_offset(p, q, h.Qs);
+    g.u = h.su + so;
+    g.bx = h.sbx + so;
+    g.by = h.sby + so;
+    bool hx = p < h.pi, hy = q < h.qi;  // parents inside the item's hierarchy
+    g.bmode = (!hx && !hy) ? 0 : (hx && hy) ? 2 : (hx ? 0 : 1);
+    g.ax = h.ax + co;
+    g.ay = h.ay + co;
+    g.nx = 1 << p;
+    g.ny = 1 << q;
+    return g;
+}
+
+// Visit halves of Algorithm 1 on one grid (p,q) of an item's hierarchy.
+template <class T>
+__device__ void visit_pre(const Hier<T>& h, int p, int q, int zero_init, int nu1)
+{
+    GView<T> g = view_of(h, p, q);
+    if (p == 1 && q == 1) { cta_coarsest(g); return; }
+    if (zero_init) { cta_zero(g); __syncthreads(); }
+    cta_smooth(g, nu1);
+    T* cxb = (p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
+    T* cyb = (q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
+    cta_restrict(g, cxb, cyb);
+}
+
+template <class T>
+__device__ void visit_post(const Hier<T>& h, int p, int q, int nu2, T omega)
+{
+    if (p == 1 && q == 1) return;
+    GView<T> g = view_of(h, p, q);
+    const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
+    const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
+    cta_prolong(g, ucx, ucy, omega);
+    cta_smooth(g, nu2);
+}
+
+struct CycleParams {
+    int mu, nu1, nu2;
+    double omega;
+};
+
+// Grids of diagonal d of the hierarchy below (pi, qi).
+__device__ __forceinline__ void diag_range(int d, int pi, int qi, int& plo, int& phi)
+{
+    plo = max(1, d + 2 - qi);
+    phi = min(pi, d + 1);
+}
+
+// mu-cycle (Algorithm 1) on diagonals <= d of one item's hierarchy, run by one CTA.
+template <class T>
+__device__ void cta_mu_cycle(const Hier<T>& h, int d, int zero_init, const CycleParams& cp)
+{
+    // explicit stack of (d, phase, k, zero_init): phase 0 = PRE, 1 = children, 2 = POST
+    int sd[24], sk[24], sz[24], sp[24];
+    int top = 0;
+    sd[0] = d; sk[0] = 0; sz[0] = zero_init; sp[0] = 0;
+    while (top >= 0) {
+        int cd = sd[top];
+        int plo, phi;
+        diag_range(cd, h.pi, h.qi, plo, phi);
+        if (sp[top] == 0) {
+            for (int p = plo; p <= phi; ++p) visit_pre(h, p, cd + 2 - p, sz[top], cp.nu1);
+            if (cd == 0) { --top; continue; }
+            sp[top] = 1;
+            sk[top] = 0;
+        }
+        if (sp[top] == 1) {
+            if (sk[top] < cp.mu) {
+                int zi = (sk[top] == 0);
+                sk[top] += 1;
+                ++top;
+                sd[top] = cd - 1; sk[top] = 0; sz[top] = zi; sp[top] = 0;
+                continue;
+            }
+            sp[top] = 2;
+        }
+        for (int p = plo; p <= phi; ++p) visit_post(h, p, cd + 2 - p, cp.nu2, (T)cp.omega);
+        --top;
+    }
+}
+
+// ----------------------------------------------------------------- kernels --
+
+template <class T>
+__device__ __forceinline__ Hier<T> hier_of(const DevCtx& cx, const TaskRef& t, T* su, T* sbx, T* sby, const T* ax,
+                                           const T* ay)
+{
+    const SampleInfo& S = cx.samples[t.s];
+    Hier<T> h;
+    h.su = su; h.sbx = sbx; h.sby = sby;
+    h.ax = ax + S.node_off; h.ay = ay + S.node_off;
+    h.Ps = S.P; h.Qs = S.Q;
+    h.pi = t.seg->pi; h.qi = t.seg->qi;
+    h.scr = t.scr;
+    return h;
+}
+
+template <class T>
+__global__ void k_pre(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init,
+                      int nu1)
+{
+    TaskRef t = resolve(cx);
+    if (!active[t.item]) return;
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    visit_pre(h, t.seg->p, t.seg->q, zero_init, nu1);
+}
+
+template <class T>
+__global__ void k_post(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2,
+                       double omega)
+{
+    TaskRef t = resolve(cx);
+    if (!active[t.item]) return;
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    visit_post(h, t.seg->p, t.seg->q, nu2, (T)omega);
+}
+
+template <class T>
+__global__ void k_low(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int d,
+                      int calls, int zero_init, CycleParams cp)
+{
+    TaskRef t = resolve(cx);
+    if (!active[t.item]) return;
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    for (int c = 0; c < calls; ++c) cta_mu_cycle(h, d, c == 0 ? zero_init : 0, cp);
+}
+
+// Coefficients on every grid: a = exp(Z) at face midpoints (field node of
+// G^(P+1,Q+1) given in the header), scaled by 1/dx^2 and 1/dy^2.
+__global__ void k_coeffs(DevCtx cx, const double* Z, double* ax64, double* ay64, float* ax32, float* ay32)
+{
+    TaskRef t = resolve(cx);
+    const SampleInfo& S = cx.samples[t.s];
+    const int p = t.seg->p, q = t.seg->q, nx = 1 << p, ny = 1 << q, W = nx + 1;
+    const int NFx = (1 << (S.P + 1)) + 1, sx = 1 << (S.P - p), sy = 1 << (S.Q - q);
+    const double idx2 = (double)nx * nx, idy2 = (double)ny * ny;
+    const double* Zs = Z + S.field_off;
+    const int64_t off = S.node_off + grid_offset(p, q, S.Q);
+    const int n = (nx + 1) * (ny + 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = k % W, j = k / W;
+        double vx = 0.0, vy = 0.0;
+        if (i < nx) vx = exp(Zs[(int64_t)(2 * j * sy) * NFx + (2 * i + 1) * sx]) * idx2;
+        if (j < ny) vy = exp(Zs[(int64_t)((2 * j + 1) * sy) * NFx + 2 * i * sx]) * idy2;
+        ax64[off + k] = vx;
+        ay64[off + k] = vy;
+        if (ax32) {
+            ax32[off + k] = (float)vx;
+            ay32[off + k] = (float)vy;
+        }
+    }
+}
+
+// FMSG initial guess of an item (Algorithm 2): u = kappa_x Pc_x sol(p-1,q) +
+// kappa_y Pc_y sol(p,q-1) with cubic Pc (odd-reflection boundary stencil);
+// one child only on the q = 1 or p = 1 edge; u = 0 on G^(1,1).
+__device__ __forceinline__ double cubic_at(const double* c, int stride, int m, int k)
+{
+    double cm1 = (k - 1 >= 0) ? c[(k - 1) * stride] : -c[stride];
+    double c0 = c[k * stride];
+    double c1 = c[(k + 1) * stride];
+    double c2 = (k + 2 <= m) ? c[(k + 2) * stride] : -c[(m - 1) * stride];
+    return (-cm1 + 9.0 * c0 + 9.0 * c1 - c2) / 16.0;
+}
+
+__global__ void k_interp(DevCtx cx, double* u64, const double* ax64, const double* ay64)
+{
+    TaskRef t = resolve(cx);
+    const SampleInfo& S = cx.samples[t.s];
+    const int p = t.seg->pi, q = t.seg->qi, nx = 1 << p, ny = 1 << q, W = nx + 1;
+    double* u = u64 + S.node_off + grid_offset(p, q, S.Q);
+    const double* ax = ax64 + S.node_off + grid_offset(p, q, S.Q);
+    const double* ay = ay64 + S.node_off + grid_offset(p, q, S.Q);
+    const double* ucx = (p > 1) ? u64 + S.node_off + grid_offset(p - 1, q, S.Q) : nullptr;
+    const double* ucy = (q > 1) ? u64 + S.node_off + grid_offset(p, q - 1, S.Q) : nullptr;
+    const int n = (nx - 1) * (ny - 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = 1 + k % (nx - 1), j = 1 + k / (nx - 1);
+        int c = j * W + i;
+        if (!ucx && !ucy) { u[c] = 0.0; continue; }
+        double vx = 0.0, vy = 0.0;
+        if (ucx) {
+            const int Wc = (nx >> 1) + 1;
+            vx = (i & 1) ? cubic_at(ucx + j * Wc, 1, nx >> 1, i >> 1) : ucx[j * Wc + (i >> 1)];
+        }
+        if (ucy) vy = (j & 1) ? cubic_at(ucy + i, W, ny >> 1, j >> 1) : ucy[(j >> 1) * W + i];
+        double corr;
+        if (ucx && ucy) {
+            double cxv = ax[c - 1] + ax[c], cyv = ay[c - W] + ay[c];
+            double x2 = cxv * cxv, y2 = cyv * cyv;
+            corr = (x2 / (x2 + y2)) * vx + (y2 / (x2 + y2)) * vy;
+        } else {
+            corr = ucx ? vx : vy;
+        }
+        u[c] = corr;
+    }
+}
+
+// Block reduction of a double in a fixed order (result valid on thread 0).
+__device__ double block_sum(double v)
+{
+    __shared__ double warp_part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) warp_part[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) s += warp_part[k];
+    }
+    return s;
+}
+
+// FP64 residual of the item's grid, convergence decision, and the right-hand
+// side of the next correction cycle (written into the item's scratch).
+template <class T>
+__global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, const double* ay64, T* sbx, int step,
+                           int max_cycles, double eps, int* active, int* cycles, double* relres, int* status,
+                           int* counter)
+{
+    TaskRef t = resolve(cx);
+    const SampleInfo& S = cx.samples[t.s];
+    const int p = t.seg->pi, q = t.seg->qi, nx = 1 << p, ny = 1 << q, W = nx + 1;
+    const int64_t off = S.node_off + grid_offset(p, q, S.Q);
+    const double* u = u64 + off;
+    const double* ax = ax64 + off;
+    const double* ay = ay64 + off;
+    T* rb = sbx + t.scr + grid_offset(p, q, q);
+    if (step > 0 && !active[t.item]) return;  // finished earlier
+    const int n = (nx - 1) * (ny - 1);
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = 1 + k % (nx - 1), j = 1 + k / (nx - 1);
+        int c = j * W + i;
+        double aw = ax[c - 1], ae = ax[c], as = ay[c - W], an = ay[c];
+        double Au = (aw + ae + as + an) * u[c] - (aw * u[c - 1] + ae * u[c + 1]) - (as * u[c - W] + an * u[c + W]);
+        double r = 1.0 - Au;
+        acc += r * r;
+        rb[c] = (T)r;
+    }
+    double ss = block_sum(acc);
+    if (threadIdx.x == 0) {
+        double rr = sqrt(ss / (double)n);  // ||b|| with b = 1 on n interior nodes
+        int act;
+        if (step == 0) act = 1;  // at least one cycle
+        else if (!(rr == rr) || isinf(rr)) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NONFINITE); }
+        else if (rr <= eps) act = 0;
+        else if (step >= max_cycles) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED); }
+        else act = 1;
+        active[t.item] = act;
+        if (!act) {
+            cycles[t.item] = step;
+            relres[t.item] = rr;
+        } else {
+            atomicAdd(counter, 1);
+        }
+    }
+}
+
+template <class T>
+__global__ void k_update(DevCtx cx, double* u64, const T* su, const int* active)
+{
+    TaskRef t = resolve(cx);
+    if (!active[t.item]) return;
+    const SampleInfo& S = cx.samples[t.s];
+    const int p = t.seg->pi, q = t.seg->qi, nx = 1 << p, ny = 1 << q, W = nx + 1;
+    double* u = u64 + S.node_off + grid_offset(p, q, S.Q);
+    const T* e = su + t.scr + grid_offset(p, q, q);
+    const int n = (nx - 1) * (ny - 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = 1 + k % (nx - 1), j = 1 + k / (nx - 1);
+        int c = j * W + i;
+        u[c] += (double)e[c];
+    }
+}
+
+// QoI of the item's converged grid (Sec. 4).
+__global__ void k_qoi(DevCtx cx, const double* u64, const double* Z, int qoi, double* Qout)
+{
+    TaskRef t = resolve(cx);
+    const SampleInfo& S = cx.samples[t.s];
+    const int p = t.seg->pi, q = t.seg->qi, nx = 1 << p, ny = 1 << q, W = nx + 1;
+    const double* u = u64 + S.node_off + grid_offset(p, q, S.Q);
+    const double dx = 1.0 / nx, dy = 1.0 / ny;
+    double acc = 0.0;
+    if (qoi == MSG_QOI_INTEGRAL) {
+        const int n = (nx - 1) * (ny - 1);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int i = 1 + k % (nx - 1), j = 1 + k / (nx - 1);
+            acc += u[j * W + i];
+        }
+        double s = block_sum(acc);
+        if (threadIdx.x == 0) Qout[t.item] = dx * dy * s;
+    } else if (qoi == MSG_QOI_POINT) {
+        if (threadIdx.x == 0) Qout[t.item] = u[(ny / 2) * W + nx / 2];
+    } else if (qoi == MSG_QOI_SUBDOMAIN) {
+        if (p < 2 || q < 2) {
+            if (threadIdx.x == 0) Qout[t.item] = nan("");
+            return;
+        }
+        const int i0 = nx / 4, i1 = nx / 2, j0 = ny / 4, j1 = ny / 2, wi = i1 - i0 + 1;
+        const int n = wi * (j1 - j0 + 1);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int i = i0 + k % wi, j = j0 + k / wi;
+            double w = ((i == i0 || i == i1) ? 0.5 : 1.0) * ((j == j0 || j == j1) ? 0.5 : 1.0);
+            acc += w * u[j * W + i];
+        }
+        double s = block_sum(acc);
+        if (threadIdx.x == 0) Qout[t.item] = s * dx * dy / (0.25 * 0.25);
+    } else {  // flux through x = 1
+        const int NFx = (1 << (S.P + 1)) + 1, sy = 1 << (S.Q - q);
+        const double* Zs = Z + S.field_off;
+        for (int j = 1 + threadIdx.x; j < ny; j += blockDim.x) {
+            double a = exp(Zs[(int64_t)(2 * j * sy) * NFx + (NFx - 1)]);
+            acc += a * u[j * W + nx - 1] / dx;
+        }
+        double s = block_sum(acc);
+        if (threadIdx.x == 0) Qout[t.item] = dy * s;
+    }
+}
+
+// ------------------------------------------------------------------ plan --
+
+namespace {
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+struct Plan {
+    int S = 0;
+    std::vector<SampleInfo> samples;
+    std::vector<int> perm;
+    std::vector<Group> groups;  // scr_start / scr_per_sample are per stage (see stage_groups)
+    int Lmax = -1;
+    // per stage L: group tables with the stage's scratch layout
+    std::vector<std::vector<Group>> stage_groups;
+    // segment lists: coefficient/qoi over all grids; per (L, d) task lists; per L item lists
+    std::vector<Segment> all_segs;  // (g, pi=p, qi=q, p, q) over all grids
+    std::vector<std::vector<std::vector<Segment>>> task_segs;  // [L][d]
+    int64_t total_nodes = 0, total_field = 0, total_q = 0, scratch_nodes = 0;
+    // device offsets of each segment list in the table area
+    size_t table_bytes = 0;
+};
+
+int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
+{
+    if (S < 0) { set_error("S < 0"); return MSG_ERR_INVALID; }
+    if (S > 0 && !PQ) { set_error("PQ is NULL"); return MSG_ERR_INVALID; }
+    if (!prm) { set_error("params is NULL"); return MSG_ERR_INVALID; }
+    if (prm->mu < 1 || prm->mu > 3 || prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 ||
+        prm->max_cycles < 1 || !(prm->eps >= 0.0) || !(prm->omega > 0.0) || prm->omega > 2.0) {
+        set_error("invalid solver parameters");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->precision != MSG_PREC_FP64 && prm->precision != MSG_PREC_MIXED) {
+        set_error("precision must be MSG_PREC_FP64 or MSG_PREC_MIXED");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->qoi < 0 || prm->qoi > 3) { set_error("qoi out of range"); return MSG_ERR_INVALID; }
+    for (int64_t i = 0; i < S; ++i) {
+        if (PQ[2 * i] < 1 || PQ[2 * i] > 12 || PQ[2 * i + 1] < 1 || PQ[2 * i + 1] > 12) {
+            set_error("grid exponents must satisfy 1 <= P, Q <= 12");
+            return MSG_ERR_INVALID;
+        }
+    }
+    return MSG_OK;
+}
+
+void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
+{
+    pl.S = (int)S;
+    pl.samples.resize(S);
+    std::map<std::pair<int, int>, int> gid;
+    std::vector<int> sample_group(S);
+    for (int64_t i = 0; i < S; ++i) {
+        SampleInfo& si = pl.samples[i];
+        si.P = PQ[2 * i];
+        si.Q = PQ[2 * i + 1];
+        si.node_off = pl.total_nodes;
+        si.field_off = pl.total_field;
+        si.q_off = pl.total_q;
+        pl.total_nodes += rect_nodes(si.P, si.Q);
+        pl.total_field += field_nodes(si.P, si.Q);
+        pl.total_q += (int64_t)si.P * si.Q;
+        auto key = std::make_pair(si.P, si.Q);
+        auto it = gid.find(key);
+        if (it == gid.end()) {
+            int g = (int)pl.groups.size();
+            gid[key] = g;
+            Group G{};
+            G.P = si.P; G.Q = si.Q;
+            pl.groups.push_back(G);
+            sample_group[i] = g;
+        } else {
+            sample_group[i] = it->second;
+        }
+        pl.Lmax = std::max(pl.Lmax, si.P + si.Q - 2);
+    }
+    // perm: samples ordered by group
+    std::vector<int> cnt(pl.groups.size(), 0);
+    for (int64_t i = 0; i < S; ++i) cnt[sample_group[i]]++;
+    int acc = 0;
+    for (size_t g = 0; g < pl.groups.size(); ++g) {
+        pl.groups[g].start = acc;
+        pl.groups[g].count = cnt[g];
+        acc += cnt[g];
+        cnt[g] = pl.groups[g].start;
+    }
+    pl.perm.resize(S);
+    for (int64_t i = 0; i < S; ++i) pl.perm[cnt[sample_group[i]]++] = (int)i;
+
+    // all-grid segments (coefficients)
+    int64_t blk = 0;
+    for (size_t g = 0; g < pl.groups.size(); ++g)
+        for (int p = 1; p <= pl.groups[g].P; ++p)
+            for (int q = 1; q <= pl.groups[g].Q; ++q) {
+                Segment sg{(int)g, p, q, p, q, blk, 0};
+                pl.all_segs.push_back(sg);
+                blk += pl.groups[g].count;
+            }
+
+    // stages
+    pl.stage_groups.assign(pl.Lmax + 1, pl.groups);
+    pl.task_segs.assign(pl.Lmax + 1, {});
+    for (int L = 0; L <= pl.Lmax; ++L) {
+        std::vector<Group>& sg = pl.stage_groups[L];
+        int64_t scr = 0;
+        std::vector<std::vector<int64_t>> slot(pl.groups.size());
+        for (size_t g = 0; g < sg.size(); ++g) {
+            int64_t per = 0;
+            for (int p = 1; p <= sg[g].P; ++p) {
+                int q = L + 2 - p;
+                if (q < 1 || q > sg[g].Q) continue;
+                slot[g].push_back(per);
+                per += rect_nodes(p, q);
+            }
+            sg[g].scr_start = scr;
+            sg[g].scr_per_sample = per;
+            scr += per * sg[g].count;
+        }
+        pl.scratch_nodes = std::max(pl.scratch_nodes, scr);
+        pl.task_segs[L].assign(L + 1, {});
+        for (int d = 0; d <= L; ++d) {
+            int64_t b = 0;
+            std::vector<Segment>& v = pl.task_segs[L][d];
+            for (size_t g = 0; g < sg.size(); ++g) {
+                int k = 0;
+                for (int pi = 1; pi <= sg[g].P; ++pi) {
+                    int qi = L + 2 - pi;
+                    if (qi < 1 || qi > sg[g].Q) continue;
+                    for (int p = std::max(1, d + 2 - qi); p <= std::min(pi, d + 1); ++p) {
+                        Segment s{(int)g, pi, qi, p, d + 2 - p, b, slot[g][k]};
+                        v.push_back(s);
+                        b += sg[g].count;
+                    }
+                    ++k;
+                }
+            }
+        }
+    }
+}
+
+struct WsLayout {
+    size_t samples, perm, groups, segs, nsegs_total;
+    size_t active, cycles_i, relres_i, counter;
+    size_t u64, ax64, ay64, ax32, ay32, su, sbx, sby;
+    size_t total;
+};
+
+WsLayout layout_of(const Plan& pl, int precision)
+{
+    WsLayout w{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    size_t nseg = pl.all_segs.size();
+    for (int L = 0; L <= pl.Lmax; ++L)
+        for (int d = 0; d <= L; ++d) nseg += pl.task_segs[L][d].size();
+    w.nsegs_total = nseg;
+    w.samples = take(sizeof(SampleInfo) * std::max<int64_t>(pl.S, 1));
+    w.perm = take(sizeof(int) * std::max<int64_t>(pl.S, 1));
+    w.groups = take(sizeof(Group) * std::max<size_t>(1, pl.groups.size() * (pl.Lmax + 2)));
+    w.segs = take(sizeof(Segment) * std::max<size_t>(nseg, 1));
+    w.active = take(sizeof(int) * std::max<int64_t>(pl.total_q, 1));
+    w.cycles_i = take(sizeof(int) * std::max<int64_t>(pl.total_q, 1));
+    w.relres_i = take(sizeof(double) * std::max<int64_t>(pl.total_q, 1));
+    w.counter = take(sizeof(int) * 4);
+    w.u64 = take(sizeof(double) * pl.total_nodes);
+    w.ax64 = take(sizeof(double) * pl.total_nodes);
+    w.ay64 = take(sizeof(double) * pl.total_nodes);
+    size_t es = precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    if (precision == MSG_PREC_MIXED) {
+        w.ax32 = take(sizeof(float) * pl.total_nodes);
+        w.ay32 = take(sizeof(float) * pl.total_nodes);
+    }
+    w.su = take(es * pl.scratch_nodes);
+    w.sbx = take(es * pl.scratch_nodes);
+    w.sby = take(es * pl.scratch_nodes);
+    w.total = off + 256;
+    return w;
+}
+
+int lowcut(int precision) { return precision == MSG_PREC_MIXED ? 6 : 6; }
+
+constexpr int kThreads = 256;
+
+template <class T>
+struct Runner {
+    const Plan& pl;
+    const WsLayout& wl;
+    char* ws;
+    cudaStream_t st;
+    const msg_params& prm;
+    DevCtx base;            // samples, perm filled in
+    const Group* dgroups;   // device stage group tables
+    const Segment* dsegs;   // device segments
+    std::vector<size_t> seg_index;  // start index of each list in dsegs
+    T* su; T* sbx; T* sby;
+    const T* ax; const T* ay;
+    int* active;
+    CycleParams cp;
+
+    DevCtx ctx(const Group* groups, const Segment* segs, int nseg) const
+    {
+        DevCtx c = base;
+        c.groups = groups;
+        c.segs = segs;
+        c.nseg = nseg;
+        return c;
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------- entry point --
+
+template <class T>
+static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_params& prm, const double* Z,
+                     double* Qout, int32_t* status, int32_t* cycles_out, double* relres_out, cudaStream_t st)
+{
+    // ---- upload tables
+    std::vector<Segment> segs;
+    std::vector<size_t> all_idx(1, 0);
+    segs.insert(segs.end(), pl.all_segs.begin(), pl.all_segs.end());
+    std::vector<std::vector<size_t>> tidx(pl.Lmax + 1);
+    for (int L = 0; L <= pl.Lmax; ++L) {
+        tidx[L].resize(L + 1);
+        for (int d = 0; d <= L; ++d) {
+            tidx[L][d] = segs.size();
+            segs.insert(segs.end(), pl.task_segs[L][d].begin(), pl.task_segs[L][d].end());
+        }
+    }
+    std::vector<Group> gtab;  // [0]: plain groups, [1+L]: stage L groups
+    gtab.insert(gtab.end(), pl.groups.begin(), pl.groups.end());
+    for (int L = 0; L <= pl.Lmax; ++L) gtab.insert(gtab.end(), pl.stage_groups[L].begin(), pl.stage_groups[L].end());
+    const size_t ng = pl.groups.size();
+
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.samples, pl.samples.data(), sizeof(SampleInfo) * pl.S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.perm, pl.perm.data(), sizeof(int) * pl.S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.groups, gtab.data(), sizeof(Group) * gtab.size(), cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.segs, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, st));
+
+    const bool mixed = prm.precision == MSG_PREC_MIXED;
+    double* u64 = (double*)(ws + wl.u64);
+    double* ax64 = (double*)(ws + wl.ax64);
+    double* ay64 = (double*)(ws + wl.ay64);
+    float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
+    float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
+    T* su = (T*)(ws + wl.su);
+    T* sbx = (T*)(ws + wl.sbx);
+    T* sby = (T*)(ws + wl.sby);
+    const T* ax = mixed ? (const T*)ax32 : (const T*)ax64;
+    const T* ay = mixed ? (const T*)ay32 : (const T*)ay64;
+    int* active = (int*)(ws + wl.active);
+    int* cyc = (int*)(ws + wl.cycles_i);
+    double* rel = (double*)(ws + wl.relres_i);
+    int* counter = (int*)(ws + wl.counter);
+    const Segment* dsegs = (const Segment*)(ws + wl.segs);
+    const Group* dgroups = (const Group*)(ws + wl.groups);
+
+    // per-sample status: caller's array or a private copy
+    int32_t* stat = status;
+    std::vector<int32_t> zero_status;
+    if (!stat) return (set_error("internal: status buffer missing"), MSG_ERR_INVALID);
+    MSG_CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(int32_t) * pl.S, st));
+    MSG_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * pl.total_nodes, st));
+    MSG_CUDA_TRY(cudaMemsetAsync(su, 0, sizeof(T) * pl.scratch_nodes, st));
+    MSG_CUDA_TRY(cudaMemsetAsync(active, 0, sizeof(int) * std::max<int64_t>(pl.total_q, 1), st));
+
+    DevCtx base{};
+    base.samples = (const SampleInfo*)(ws + wl.samples);
+    base.perm = (const int*)(ws + wl.perm);
+    auto ctx = [&](const Group* g, size_t seg0, size_t n) {
+        DevCtx c = base;
+        c.groups = g;
+        c.segs = dsegs + seg0;
+        c.nseg = (int)n;
+        return c;
+    };
+    auto nblocks = [&](const std::vector<Segment>& v, const std::vector<Group>& gt) -> int64_t {
+        if (v.empty()) return 0;
+        return v.back().blk_start + gt[v.back().g].count;
+    };
+
+    // coefficients on every grid
+    {
+        int64_t nb = nblocks(pl.all_segs, pl.groups);
+        if (nb > 0) {
+            k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(ctx(dgroups, 0, pl.all_segs.size()), Z, ax64, ay64, ax32, ay32);
+            MSG_CHECK_LAUNCH();
+        }
+    }
+
+    const int dcut = lowcut(prm.precision);
+    CycleParams cp{prm.mu, prm.nu1, prm.nu2, prm.omega};
+    int* hcount = nullptr;
+    MSG_CUDA_TRY(cudaMallocHost(&hcount, sizeof(int)));  // pinned flag readback
+    struct PinnedFree { int* p; ~PinnedFree() { if (p) cudaFreeHost(p); } } pf{hcount};
+
+    for (int L = 0; L <= pl.Lmax; ++L) {
+        const Group* sg = dgroups + ng * (1 + L);
+        const std::vector<Group>& hsg = pl.stage_groups[L];
+        const std::vector<Segment>& items = pl.task_segs[L][L];
+        int64_t nit = nblocks(items, hsg);
+        if (nit == 0) continue;
+        DevCtx ic = ctx(sg, tidx[L][L], items.size());
+        k_interp<<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, ax64, ay64);
+        MSG_CHECK_LAUNCH();
+        for (int step = 0;; ++step) {
+            MSG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+            k_residual<T><<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, ax64, ay64, sbx, step, prm.max_cycles, prm.eps,
+                                                             active, cyc, rel, stat, counter);
+            MSG_CHECK_LAUNCH();
+            MSG_CUDA_TRY(cudaMemcpyAsync(hcount, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MSG_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*hcount == 0) break;
+            // one mu-cycle of every active item: recursive launch schedule
+            struct Emitter {
+                int L, dcut, mu;
+                std::vector<std::pair<int, std::vector<int>>> ops;  // unused
+            };
+            // recursive lambda through std::function-free helper
+            int err = MSG_OK;
+            auto launch_low = [&](int d, int calls, int zi) {
+                DevCtx c = ic;
+                k_low<T><<<(unsigned)nit, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, d, calls, zi, cp);
+                if (cudaGetLastError() != cudaSuccess) err = MSG_ERR_CUDA;
+            };
+            auto launch_half = [&](int d, int pre, int zi) {
+                const std::vector<Segment>& v = pl.task_segs[L][d];
+                int64_t nb = nblocks(v, hsg);
+                if (nb == 0) return;
+                DevCtx c = ctx(sg, tidx[L][d], v.size());
+                if (pre) k_pre<T><<<(unsigned)nb, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, zi, prm.nu1);
+                else k_post<T><<<(unsigned)nb, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, prm.nu2, prm.omega);
+                if (cudaGetLastError() != cudaSuccess) err = MSG_ERR_CUDA;
+            };
+            // iterative emission of the recursion of Algorithm 1 above dcut
+            struct Frame { int d, k, zi, phase; };
+            std::vector<Frame> stack;
+            if (L <= dcut) {
+                launch_low(L, 1, 1);
+            } else {
+                stack.push_back({L, 0, 1, 0});
+                while (!stack.empty()) {
+                    Frame& f = stack.back();
+                    if (f.phase == 0) {
+                        launch_half(f.d, 1, f.zi);
+                        f.phase = 1;
+                        if (f.d - 1 <= dcut) {
+                            launch_low(f.d - 1, prm.mu, 1);
+                            f.phase = 2;
+                        }
+                        continue;
+                    }
+                    if (f.phase == 1) {
+                        if (f.k < prm.mu) {
+                            int zi = (f.k == 0);
+                            f.k += 1;
+                            stack.push_back({f.d - 1, 0, zi, 0});
+                            continue;
+                        }
+                        f.phase = 2;
+                    }
+                    launch_half(f.d, 0, 0);
+                    stack.pop_back();
+                }
+            }
+            if (err) { set_error("kernel launch failed in the cycle schedule"); return MSG_ERR_CUDA; }
+            k_update<T><<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, su, active);
+            MSG_CHECK_LAUNCH();
+        }
+        k_qoi<<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, Z, prm.qoi, Qout);
+        MSG_CHECK_LAUNCH();
+    }
+    if (cycles_out) MSG_CUDA_TRY(cudaMemcpyAsync(cycles_out, cyc, sizeof(int) * pl.total_q, cudaMemcpyDeviceToDevice, st));
+    if (relres_out) MSG_CUDA_TRY(cudaMemcpyAsync(relres_out, rel, sizeof(double) * pl.total_q, cudaMemcpyDeviceToDevice, st));
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));
+    return MSG_OK;
+}
+
+}  // namespace msg
+
+using namespace msg;
+
+extern "C" size_t msg_workspace_bytes(const int32_t* PQ, int64_t S, const msg_params* prm)
+{
+    clear_error();
+    if (validate(PQ, S, prm) != MSG_OK) return 0;
+    Plan pl;
+    build_plan(PQ, S, pl);
+    // the per-sample status array is kept inside the workspace when the caller passes none
+    return layout_of(pl, prm->precision).total + align_up(sizeof(int32_t) * std::max<int64_t>(S, 1));
+}
+
+extern "C" int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, const double* Z, double* Qout,
+                                   int32_t* status, int32_t* cycles, double* relres, void* workspace, size_t ws_bytes,
+                                   void* stream)
+{
+    clear_error();
+    int rc = validate(PQ, S, prm);
+    if (rc != MSG_OK) return rc;
+    if (S == 0) return MSG_OK;
+    if (!Z || !Qout || !workspace) { set_error("Z, Qout and workspace must be non-NULL"); return MSG_ERR_INVALID; }
+    Plan pl;
+    build_plan(PQ, S, pl);
+    WsLayout wl = layout_of(pl, prm->precision);
+    size_t need = wl.total + align_up(sizeof(int32_t) * S);
+    if (ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return MSG_ERR_WORKSPACE;
+    }
+    char* ws = (char*)workspace;
+    ws = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    if ((size_t)(ws - (char*)workspace) + need - 256 > ws_bytes) {
+        set_error("workspace too small after alignment");
+        return MSG_ERR_WORKSPACE;
+    }
+    int32_t* stat = status ? status : (int32_t*)(ws + wl.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prm->precision == MSG_PREC_MIXED)
+        return run_solve<float>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
+    return run_solve<double>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
+}

@@ -1,0 +1,205 @@
+"""Thin ctypes binding of the C ABI in ``include/msg_mimc.h``.
+
+Argument marshalling only: every step of the path runs in the CUDA library
+``libmsgmimc.so``.  Loading fails loudly when the library has not been built
+(``paper_1907_12334_gb300.build.build()``); there is no CPU fallback.
+
+Device buffers are torch tensors (PyTorch provides device memory and streams);
+the library sees raw pointers and the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MSG_OK, MSG_ERR_INVALID, MSG_ERR_WORKSPACE, MSG_ERR_CUDA, MSG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+MSG_SAMPLE_NOT_CONVERGED, MSG_SAMPLE_NONFINITE = 1, 2
+MSG_PREC_FP64, MSG_PREC_MIXED = 0, 1
+MSG_QOI_INTEGRAL, MSG_QOI_POINT, MSG_QOI_SUBDOMAIN, MSG_QOI_FLUX = 0, 1, 2, 3
+MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32 = 0, 1, 2
+
+EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
+            "msg_solve_batch", "mimc_differences", "msg_last_error", "msg_version")
+
+
+class MsgError(RuntimeError):
+    pass
+
+
+class msg_params(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+                ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32)]
+
+
+@dataclass
+class SolverParams:
+    """W(nu1,nu2) FMSG parameters (Sec. 2 numerical setup: mu=2, nu1=nu2=2)."""
+    mu: int = 2
+    nu1: int = 2
+    nu2: int = 2
+    max_cycles: int = 200
+    eps: float = 1e-10
+    omega: float = 1.0
+    precision: int = MSG_PREC_MIXED
+    qoi: int = MSG_QOI_INTEGRAL
+
+    def c(self) -> msg_params:
+        return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
+                          self.qoi)
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmsgmimc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise MsgError(f"CUDA library not built: {path} is missing (run paper_1907_12334_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64, dbl, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_double, ctypes.c_size_t)
+    L.msg_normals.argtypes = [u64, u64, i64, i32, vp, vp]
+    L.msg_normals.restype = i32
+    L.kl_prepared_bytes.argtypes = [i64, i32, i32]
+    L.kl_prepared_bytes.restype = sz
+    L.kl_prepare.argtypes = [vp, vp, i64, i32, i32, vp, sz, vp]
+    L.kl_prepare.restype = i32
+    L.sample_field.argtypes = [vp, i64, i32, i32, vp, i64, vp, i32, vp]
+    L.sample_field.restype = i32
+    L.msg_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(msg_params)]
+    L.msg_workspace_bytes.restype = sz
+    L.msg_solve_batch.argtypes = [vp, i64, ctypes.POINTER(msg_params), vp, vp, vp, vp, vp, vp, sz, vp]
+    L.msg_solve_batch.restype = i32
+    L.mimc_differences.argtypes = [vp, i64, i32, i32, vp, vp, i32, i32, vp, vp, vp]
+    L.mimc_differences.restype = i32
+    L.msg_last_error.argtypes = []
+    L.msg_last_error.restype = ctypes.c_char_p
+    L.msg_version.argtypes = []
+    L.msg_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != MSG_OK:
+        raise MsgError(f"libmsgmimc error {rc}: {load().msg_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host_i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def field_points(P: int, Q: int) -> int:
+    return ((1 << (P + 1)) + 1) * ((1 << (Q + 1)) + 1)
+
+
+# ------------------------------------------------------------------- ABI ----
+
+def msg_normals(seed: int, s0: int, S: int, M: int, xi, stream=None):
+    _check(load().msg_normals(seed, s0, S, M, _ptr(xi), _stream(stream)))
+
+
+def kl_prepared_bytes(npts: int, M: int, mode: int) -> int:
+    return int(load().kl_prepared_bytes(npts, M, mode))
+
+
+def kl_prepare(Phi, sqrt_lambda, mode: int, prepared, stream=None):
+    npts, M = Phi.shape
+    _check(load().kl_prepare(_ptr(Phi), _ptr(sqrt_lambda), npts, M, mode, _ptr(prepared),
+                             prepared.numel() * prepared.element_size(), _stream(stream)))
+
+
+def sample_field(prepared, npts: int, M: int, mode: int, xi, Z, stream=None):
+    import torch
+
+    S = xi.shape[0]
+    _check(load().sample_field(_ptr(prepared), npts, M, mode, _ptr(xi), S, _ptr(Z),
+                               1 if Z.dtype == torch.float32 else 0, _stream(stream)))
+
+
+def msg_workspace_bytes(PQ, prm: SolverParams) -> int:
+    pq = _host_i32(PQ).reshape(-1, 2)
+    c = prm.c()
+    return int(load().msg_workspace_bytes(pq.ctypes.data_as(ctypes.c_void_p), pq.shape[0], ctypes.byref(c)))
+
+
+def msg_solve_batch(PQ, prm: SolverParams, Z, Qout, status=None, cycles=None, relres=None, workspace=None,
+                    stream=None):
+    pq = _host_i32(PQ).reshape(-1, 2)
+    c = prm.c()
+    _check(load().msg_solve_batch(pq.ctypes.data_as(ctypes.c_void_p), pq.shape[0], ctypes.byref(c), _ptr(Z),
+                                  _ptr(Qout), _ptr(status), _ptr(cycles), _ptr(relres), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def mimc_differences(L, p0: int, q0: int, Q, dQ, ptau=None, Y=None, stream=None):
+    Lh = _host_i32(L).reshape(-1, 2)
+    if ptau is not None:
+        pt = np.ascontiguousarray(np.asarray(ptau, dtype=np.float64))
+        ld1, ld2 = pt.shape
+        pp = pt.ctypes.data_as(ctypes.c_void_p)
+    else:
+        ld1 = ld2 = 0
+        pp = None
+    _check(load().mimc_differences(Lh.ctypes.data_as(ctypes.c_void_p), Lh.shape[0], p0, q0, _ptr(Q), pp, ld1, ld2,
+                                   _ptr(dQ), _ptr(Y), _stream(stream)))
+
+
+def msg_version() -> str:
+    return load().msg_version().decode()
+
+
+# ------------------------------------------------------------ conveniences --
+
+def packed_sizes(PQ):
+    pq = _host_i32(PQ).reshape(-1, 2)
+    nq = int((pq[:, 0].astype(np.int64) * pq[:, 1]).sum())
+    nf = int(sum(field_points(int(P), int(Q)) for P, Q in pq))
+    return nq, nf
+
+
+def solve(PQ, Z, prm: SolverParams | None = None, stream=None):
+    """Allocate outputs + workspace with torch and run msg_solve_batch.
+
+    Returns (Q, status, cycles, relres) as device tensors (Q/cycles/relres packed per sample)."""
+    import torch
+
+    prm = prm or SolverParams()
+    pq = _host_i32(PQ).reshape(-1, 2)
+    nq, nf = packed_sizes(pq)
+    assert Z.numel() == nf and Z.dtype == torch.float64 and Z.is_cuda
+    dev = Z.device
+    Q = torch.empty(nq, dtype=torch.float64, device=dev)
+    status = torch.empty(pq.shape[0], dtype=torch.int32, device=dev)
+    cycles = torch.empty(nq, dtype=torch.int32, device=dev)
+    relres = torch.empty(nq, dtype=torch.float64, device=dev)
+    ws = torch.empty(msg_workspace_bytes(pq, prm), dtype=torch.uint8, device=dev)
+    msg_solve_batch(pq, prm, Z, Q, status, cycles, relres, ws, stream)
+    return Q, status, cycles, relres

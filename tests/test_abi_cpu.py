@@ -1,0 +1,102 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every function declared in include/*.h, and its host-side argument logic
+rejects bad input before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1907_12334_gb300 import build, msg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return msg.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("msg_normals", "kl_prepare", "sample_field", "msg_workspace_bytes", "msg_solve_batch",
+              "mimc_differences", "msg_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(msg.EXPORTED) <= set(declared_functions())
+
+
+def test_library_is_built_for_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_and_error_strings(lib):
+    assert "sm_103a" in msg.msg_version()
+    assert lib.msg_last_error() == b""
+
+
+def _ws(PQ, **kw):
+    return msg.msg_workspace_bytes(np.array(PQ, dtype=np.int32).reshape(-1, 2), msg.SolverParams(**kw))
+
+
+def test_workspace_bytes_host_logic(lib):
+    one = _ws([[3, 3]])
+    two = _ws([[3, 3], [3, 3]])
+    assert one > 0 and two > one
+    assert _ws([[8, 8]]) > _ws([[8, 7]]) > _ws([[7, 7]])
+    # FP64 cycles keep 8-byte scratch and no FP32 coefficient copy
+    assert _ws([[6, 6]], precision=msg.MSG_PREC_FP64) != _ws([[6, 6]], precision=msg.MSG_PREC_MIXED)
+    # uneven batch is the sum of its parts up to table overhead
+    mix = _ws([[2, 5], [6, 3], [1, 1]])
+    assert mix > _ws([[6, 3]])
+
+
+@pytest.mark.parametrize("PQ,kw", [([[0, 3]], {}), ([[3, 13]], {}), ([[3, 3]], {"mu": 0}),
+                                    ([[3, 3]], {"max_cycles": 0}), ([[3, 3]], {"omega": 0.0}),
+                                    ([[3, 3]], {"precision": 7}), ([[3, 3]], {"qoi": 9}),
+                                    ([[3, 3]], {"eps": float("nan")})])
+def test_invalid_arguments_rejected_on_host(lib, PQ, kw):
+    assert _ws(PQ, **kw) == 0
+    assert lib.msg_last_error() != b""
+    pq = np.array(PQ, dtype=np.int32)
+    c = msg.SolverParams(**kw).c()
+    rc = lib.msg_solve_batch(pq.ctypes.data_as(ctypes.c_void_p), 1, ctypes.byref(c), None, None, None, None, None,
+                             None, 0, None)
+    assert rc == msg.MSG_ERR_INVALID
+
+
+def test_empty_batch_is_a_no_op(lib):
+    c = msg.SolverParams().c()
+    assert lib.msg_solve_batch(None, 0, ctypes.byref(c), None, None, None, None, None, None, 0, None) == msg.MSG_OK
+    assert lib.msg_normals(0, 0, 0, 4, None, None) == msg.MSG_OK
+    assert lib.msg_normals(0, 0, 3, 0, None, None) == msg.MSG_ERR_INVALID
+
+
+def test_kl_prepared_bytes(lib):
+    assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_FP64) >= 100 * 16 * 8
+    assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_FP32) >= 100 * 16 * 4
+    assert msg.kl_prepared_bytes(100, 16, 99) == 0
+
+
+def test_mimc_rejects_bad_indices(lib):
+    L = np.array([[2, 15]], dtype=np.int32)
+    rc = lib.mimc_differences(L.ctypes.data_as(ctypes.c_void_p), 1, 1, 1, ctypes.c_void_p(8), None, 0, 0,
+                              ctypes.c_void_p(8), None, None)
+    assert rc == msg.MSG_ERR_INVALID
