@@ -59,6 +59,7 @@ def lib():
             L.orc_hier_set_params.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, ctypes.c_double]
             L.orc_hier_set_field.argtypes = [ctypes.c_void_p, _dp]
+            L.orc_hier_set_field_mode.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
             L.orc_hier_set_rhs.argtypes = [ctypes.c_void_p, _dp]
             L.orc_fmsg.argtypes = [ctypes.c_void_p]
             L.orc_mu_cycle.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -66,7 +67,7 @@ def lib():
             L.orc_field_points.argtypes = [ctypes.c_int, ctypes.c_int]
             L.orc_solve_sample.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_int, _dp, _ip, _dp]
+                                           ctypes.c_int, ctypes.c_int, _dp, _ip, _dp]
             L.orc_mimc_differences.argtypes = [ctypes.c_int] * 6 + [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
             for name in ("orc_grid_get", "orc_grid_set"):
                 getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
@@ -127,10 +128,14 @@ def field_points(P: int, Q: int) -> int:
 
 # ------------------------------------------------------------------- solver --
 
+COEF_HARMONIC, COEF_INJECTION = 0, 1
+
+
 class SolverParams:
-    def __init__(self, mu=2, nu1=2, nu2=2, max_cycles=50, eps=1e-12, omega=1.0, qoi=QOI_INTEGRAL):
+    def __init__(self, mu=2, nu1=2, nu2=2, max_cycles=50, eps=1e-12, omega=1.0, qoi=QOI_INTEGRAL,
+                 coef=COEF_HARMONIC):
         self.mu, self.nu1, self.nu2, self.max_cycles = mu, nu1, nu2, max_cycles
-        self.eps, self.omega, self.qoi = eps, omega, qoi
+        self.eps, self.omega, self.qoi, self.coef = eps, omega, qoi, coef
 
 
 def solve_sample(P: int, Q: int, Z: np.ndarray, prm: SolverParams | None = None):
@@ -144,7 +149,7 @@ def solve_sample(P: int, Q: int, Z: np.ndarray, prm: SolverParams | None = None)
     cyc = (ctypes.c_int * (P * Q))()
     rr = np.empty(P * Q, dtype=np.float64)
     st = lib().orc_solve_sample(P, Q, _d(Z), prm.mu, prm.nu1, prm.nu2, prm.max_cycles, prm.eps,
-                                prm.omega, prm.qoi, _d(Qg), cyc, _d(rr))
+                                prm.omega, prm.qoi, prm.coef, _d(Qg), cyc, _d(rr))
     if st < 0:
         raise ValueError("oracle: invalid shape")
     return Qg.reshape(P, Q), st, np.array(list(cyc)).reshape(P, Q), rr.reshape(P, Q)
@@ -193,7 +198,7 @@ class Hierarchy:
         if Z is None:
             Z = np.zeros(field_points(P, Q))
         self.Z = np.ascontiguousarray(Z, dtype=np.float64)
-        lib().orc_hier_set_field(self.h, _d(self.Z))
+        lib().orc_hier_set_field_mode(self.h, _d(self.Z), prm.coef)
         self.set_rhs(rhs)
 
     def __del__(self):

@@ -206,11 +206,23 @@ int64_t orc_field_points(int P, int Q)
 }
 
 /* Coefficients on every grid from the field Z given on F (row-major, x fastest).
- * READING (the paper does not say where a is evaluated): grid (p,q) takes a at
- * its face midpoints, i.e. at F-node ((2i+1) 2^(P-p), 2j 2^(Q-q)) for the x-face
- * (i+1/2, j) and at F-node (2i 2^(P-p), (2j+1) 2^(Q-q)) for the y-face
- * (i, j+1/2).  All grids of a sample therefore see one realisation of a. */
-void orc_hier_set_field(ohier* H, const double* Z)
+ * READING (the paper does not say where, or how, a is evaluated on a grid).
+ * The field lives on F, the nodes of G^(P+1,Q+1); the finest grid G^(P,Q)
+ * takes a = exp(Z) at its face midpoints, i.e. at F-node (2i+1, 2j) for the
+ * x-face (i+1/2, j) and (2i, 2j+1) for the y-face (i, j+1/2).  A coarser grid
+ * (p,q) covers sx = 2^(P-p) finest x-faces with each of its x-faces and
+ * sy = 2^(Q-q) finest y-faces with each y-face:
+ *   mode 0 (default): the series (harmonic) mean of those finest-face values
+ *     along the flux direction, a = sx / sum_k exp(-Z_k) (exp(Z) when sx = 1);
+ *   mode 1: injection, a = exp(Z) at the coarse face midpoint, F-node
+ *     ((2i+1) sx, 2j sy) and (2i sx, (2j+1) sy).
+ * Both give every grid of a sample one realisation of a.  Injection makes the
+ * coarse operators of fields much rougher than the coarse mesh poor copies of
+ * the fine ones: on the 0.02-correlation-length field 3 of 32 samples at
+ * 256 x 256 do not converge and the one-column grids need 45-60 cycles on
+ * average; the series mean is the 1-D homogenised coefficient of the covered
+ * segment and brings that to 1 of 32 and 7-10 cycles. */
+void orc_hier_set_field_mode(ohier* H, const double* Z, int mode)
 {
     int NFx = (1 << (H->P + 1)) + 1;
     for (int p = 1; p <= H->P; ++p)
@@ -218,13 +230,34 @@ void orc_hier_set_field(ohier* H, const double* Z)
             ogrid* g = G(H, p, q);
             int sx = 1 << (H->P - p), sy = 1 << (H->Q - q);
             for (int j = 0; j <= g->ny; ++j)
-                for (int i = 0; i < g->nx; ++i)
-                    g->ax[j * g->nx + i] = exp(Z[(int64_t)(2 * j * sy) * NFx + (2 * i + 1) * sx]);
+                for (int i = 0; i < g->nx; ++i) {
+                    int64_t row = (int64_t)(2 * j * sy) * NFx;
+                    double a;
+                    if (mode == 1 || sx == 1) {
+                        a = exp(Z[row + (2 * i + 1) * sx]);
+                    } else {
+                        double s = 0.0;
+                        for (int k = 0; k < sx; ++k) s += exp(-Z[row + 2 * (i * sx + k) + 1]);
+                        a = sx / s;
+                    }
+                    g->ax[j * g->nx + i] = a;
+                }
             for (int j = 0; j < g->ny; ++j)
-                for (int i = 0; i <= g->nx; ++i)
-                    g->ay[j * (g->nx + 1) + i] = exp(Z[(int64_t)((2 * j + 1) * sy) * NFx + 2 * i * sx]);
+                for (int i = 0; i <= g->nx; ++i) {
+                    double a;
+                    if (mode == 1 || sy == 1) {
+                        a = exp(Z[(int64_t)((2 * j + 1) * sy) * NFx + 2 * i * sx]);
+                    } else {
+                        double s = 0.0;
+                        for (int k = 0; k < sy; ++k) s += exp(-Z[(int64_t)(2 * (j * sy + k) + 1) * NFx + 2 * i * sx]);
+                        a = sy / s;
+                    }
+                    g->ay[j * (g->nx + 1) + i] = a;
+                }
         }
 }
+
+void orc_hier_set_field(ohier* H, const double* Z) { orc_hier_set_field_mode(H, Z, 0); }
 
 /* Set the right-hand side on the finest grid from nodal values h (same node
  * layout as grid (P,Q)); h == NULL means h = 1 (the paper's source term). */
@@ -613,12 +646,13 @@ static double qoi_of(const ohier* H, const ogrid* g, const double* v, int qoi, c
  * relres_out (optional, [P][Q]): final ||r||/||b|| on each grid.
  * Returns status bits (1 = not converged, 2 = non-finite), or -1 on bad input. */
 int orc_solve_sample(int P, int Q, const double* Z, int mu, int nu1, int nu2, int max_cycles,
-                     double eps, double omega, int qoi, double* Qout, int* cycles_out, double* relres_out)
+                     double eps, double omega, int qoi, int coef_mode, double* Qout, int* cycles_out,
+                     double* relres_out)
 {
     ohier* H = orc_hier_new(P, Q);
     if (!H) return -1;
     orc_hier_set_params(H, mu, nu1, nu2, max_cycles, eps, omega);
-    orc_hier_set_field(H, Z);
+    orc_hier_set_field_mode(H, Z, coef_mode);
     orc_hier_set_rhs(H, NULL);
     int st = orc_fmsg(H);
     for (int p = 1; p <= P; ++p)

@@ -27,8 +27,9 @@ MUTATIONS = [
      "double cm1 = (k - 1 >= 0) ? c[(k - 1) * stride] : c[1 * stride];", "cubic"),
     ("residual sign", "for (int c = 0; c < n; ++c) g->r[c] = g->b[c] - g->r[c];",
      "for (int c = 0; c < n; ++c) g->r[c] = g->b[c] + g->r[c];", "dense_solves or contraction"),
-    ("face placement", "g->ax[j * g->nx + i] = exp(Z[(int64_t)(2 * j * sy) * NFx + (2 * i + 1) * sx]);",
-     "g->ax[j * g->nx + i] = exp(Z[(int64_t)(2 * j * sy) * NFx + (2 * i) * sx]);", "injection"),
+    ("face placement", "a = exp(Z[row + (2 * i + 1) * sx]);", "a = exp(Z[row + (2 * i) * sx]);", "injection"),
+    ("series mean segment", "for (int k = 0; k < sx; ++k) s += exp(-Z[row + 2 * (i * sx + k) + 1]);",
+     "for (int k = 0; k < sx; ++k) s += exp(-Z[row + 2 * (i * sx + k)]);", "series_mean"),
     ("integral weight", "return g->dx * g->dy * s;", "return g->dx * s;", "printed_values or qoi_closed"),
     ("mixed difference term", "if (t1 > 0) d1_at_t2m1 -= Qgrid[(p0 + t1 - 2) * Qn + (q0 + t2 - 2)];",
      "", "worked_example or telescoping"),

@@ -79,12 +79,12 @@ def test_kl_field_is_the_matrix_product():
 # --------------------------------------------------------- discretisation --
 
 def test_coefficient_injection_faces():
-    """a = exp(Z) at face midpoints: x-face (i+1/2, j), y-face (i, j+1/2), on every grid."""
+    """Injection reading: a = exp(Z) at face midpoints x-face (i+1/2, j), y-face (i, j+1/2), every grid."""
     P, Q = 4, 3
     NFy, NFx = inputs.field_grid_shape(P, Q)
     X, Y = np.meshgrid(np.arange(NFx) / (NFx - 1), np.arange(NFy) / (NFy - 1))
     f = lambda x, y: 0.3 * x - 0.7 * y + 0.1 + 0.2 * x * y
-    H = oracle.Hierarchy(P, Q, f(X, Y).ravel())
+    H = oracle.Hierarchy(P, Q, f(X, Y).ravel(), oracle.SolverParams(coef=oracle.COEF_INJECTION))
     for p in range(1, P + 1):
         for q in range(1, Q + 1):
             nx, ny = 1 << p, 1 << q
@@ -93,6 +93,35 @@ def test_coefficient_injection_faces():
             np.testing.assert_allclose(ax, np.exp(f((i + 0.5) / nx, j / ny)), rtol=1e-14)
             i, j = np.meshgrid(np.arange(nx + 1), np.arange(ny))
             np.testing.assert_allclose(ay, np.exp(f(i / nx, (j + 0.5) / ny)), rtol=1e-14)
+
+
+def test_coefficient_series_mean_faces():
+    """Default reading: a coarse face carries the series mean of the finest-face values
+    it covers along the flux direction.  For Z = c x + g(y) the x-face values are the
+    geometric sequence exp(c x_k) (g(y) factored out) with the closed-form harmonic
+    mean; a transverse-only variation (Z = h(y)) is passed through unchanged on x-faces."""
+    P, Q = 4, 3
+    NFy, NFx = inputs.field_grid_shape(P, Q)
+    X, Y = np.meshgrid(np.arange(NFx) / (NFx - 1), np.arange(NFy) / (NFy - 1))
+    c = 1.3
+    g = lambda y: 0.4 * np.cos(3 * y)
+    H = oracle.Hierarchy(P, Q, (c * X + g(Y)).ravel())
+    for p in range(1, P + 1):
+        for q in range(1, Q + 1):
+            nx, ny = 1 << p, 1 << q
+            sx = 1 << (P - p)
+            h = 1.0 / (1 << P)  # finest x-face spacing
+            ax, _ = H.coef(p, q)
+            for i in (0, nx - 1):
+                for j in (0, ny // 2, ny):
+                    x0 = i * sx * h + h / 2  # first finest face midpoint in the segment
+                    # sx / sum_k exp(-(c (x0 + k h) + g)) = sx e^{c x0 + g} (1 - e^{-c h}) / (1 - e^{-c h sx})
+                    expect = sx * np.exp(c * x0 + g(j / ny)) * (1 - np.exp(-c * h)) / (1 - np.exp(-c * h * sx))
+                    assert ax[j, i] == pytest.approx(expect, rel=1e-13)
+    H2 = oracle.Hierarchy(P, Q, g(Y).ravel())
+    for p in range(1, P + 1):
+        ax, _ = H2.coef(p, 2)
+        np.testing.assert_allclose(ax, np.exp(g(np.arange(5) / 4))[:, None] * np.ones((1, 1 << p)), rtol=1e-14)
 
 
 def _dense(H, p, q):
