@@ -1,0 +1,400 @@
+"""Benchmark of the MSG-MIMC hot path on GB300.
+
+One step = one pass of the whole path over one batch of synthetic samples:
+  xi (Philox4x64-10 + Box-Muller)  ->  KL field Z = Phi diag(sqrt(lambda)) xi
+  ->  batched FMSG solve on every grid (FP32 cycles, FP64 residual/update/QoI)
+  ->  multi-index differences and Y.
+Workload: 4096 samples, finest grid 256 x 256 (all 64 semi-coarsened grids per
+sample), Matern nu = 3/2, sigma^2 = 1, correlation lengths 0.2 / 0.02, M = 400
+KL terms, QoI = integral of u, W(2,2), eps = 1e-10 per grid.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank solves its own batch (independent samples, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MSG samples/s at QoI rel err <=1e-8 vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--S", type=int, default=4096)
+    ap.add_argument("--P", type=int, default=8)
+    ap.add_argument("--Q", type=int, default=8)
+    ap.add_argument("--M", type=int, default=400)
+    ap.add_argument("--eps", type=float, default=1e-10)
+    ap.add_argument("--max-cycles", type=int, default=400)
+    ap.add_argument("--omega", type=float, default=1.0)
+    ap.add_argument("--gemm", default="fp32", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=0, help="oracle samples for the CPU baseline (0: one per core)")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"batch {a.S} samples, finest {1 << a.P}x{1 << a.Q} (all {a.P * a.Q} semi-coarsened grids each), "
+            f"Matern nu=1.5 sigma2=1 corr 0.2/0.02, KL M={a.M}, W(2,2) FMSG to eps={a.eps:g}, "
+            f"{a.precision} cycles, KL GEMM {a.gemm}")
+
+
+def geometric_ptau(n1, n2):
+    # initial law of Algorithm 3: P(L_j >= k) = exp(-r k), r = log(2)(1+4)/2
+    r = 0.5 * np.log(2.0) * 5.0
+    return np.exp(-r * (np.arange(n1)[:, None] + np.arange(n2)[None, :]))
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, n in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_throughput(a, n_samples=None, threads=None, seed=1):
+    """The oracle as it stands, one sample per thread, on the host cores."""
+    import oracle
+    from paper_1907_12334_gb300 import inputs
+
+    oracle.build()
+    threads = threads or os.cpu_count() or 1
+    n = n_samples or threads
+    Phi, sl = inputs.kl_basis(a.P, a.Q, inputs.FieldLaw(M=a.M))
+    Zs = [oracle.kl_field(Phi, sl, oracle.normals(seed, 10**6 + i, a.M)) for i in range(n)]
+    prm = oracle.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega)
+    t0 = time.time()
+    oracle.solve_batch([(a.P, a.Q)] * n, Zs, prm, threads=threads)
+    wall = time.time() - t0
+    return n / wall, threads, n, wall
+
+
+def reference_arm(a, rank, world):
+    if rank != 0:
+        return
+    per_step = a.cpu_samples or (os.cpu_count() or 1)
+    for _ in range(a.warmup):
+        oracle_throughput(a, n_samples=per_step)
+    vals, walls = [], []
+    for _ in range(a.steps):
+        v, cores, n, wall = oracle_throughput(a, n_samples=per_step)
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * float(np.mean(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a) + "; reference arm: scalar FP64 CPU oracle",
+                   "samples_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} FMSG solves at {1 << a.P}x{1 << a.Q} per step, one per thread"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm --
+
+def ours(a, rank, world, local_rank):
+    import torch
+
+    from paper_1907_12334_gb300 import build, inputs, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    S, P, Q, M = a.S, a.P, a.Q, a.M
+    gemm = {"fp64": msg.MSG_GEMM_FP64, "fp32": msg.MSG_GEMM_FP32, "bf16x3": msg.MSG_GEMM_BF16X3}[a.gemm]
+    prec = msg.MSG_PREC_MIXED if a.precision == "mixed" else msg.MSG_PREC_FP64
+    prm = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega, precision=prec)
+
+    # ---- set-up (untimed): KL basis, prepared basis, buffers, workspace
+    Phi, sl = inputs.kl_basis(P, Q, inputs.FieldLaw(M=M))
+    npts = Phi.shape[0]
+    Phi_d = torch.from_numpy(np.ascontiguousarray(Phi)).to(dev)
+    sl_d = torch.from_numpy(np.array(sl)).to(dev)
+    prep = torch.empty(msg.kl_prepared_bytes(npts, M, gemm), dtype=torch.uint8, device=dev)
+    msg.kl_prepare(Phi_d, sl_d, gemm, prep)
+    del Phi_d
+    PQ = np.array([[P, Q]] * S, dtype=np.int32)
+    nq = S * P * Q
+    xi = torch.empty((S, M), dtype=torch.float64, device=dev)
+    Z = torch.empty((S, npts), dtype=torch.float64, device=dev)
+    Qout = torch.empty(nq, dtype=torch.float64, device=dev)
+    status = torch.empty(S, dtype=torch.int32, device=dev)
+    cycles = torch.empty(nq, dtype=torch.int32, device=dev)
+    relres = torch.empty(nq, dtype=torch.float64, device=dev)
+    ws = torch.empty(msg.msg_workspace_bytes(PQ, prm), dtype=torch.uint8, device=dev)
+    p0 = q0 = 1
+    Lidx = np.array([[P - p0, Q - q0]] * S, dtype=np.int32)
+    ptau = geometric_ptau(P - p0 + 1, Q - q0 + 1)
+    nd = S * (P - p0 + 1) * (Q - q0 + 1)
+    dQ = torch.empty(nd, dtype=torch.float64, device=dev)
+    Y = torch.empty(S, dtype=torch.float64, device=dev)
+    seed = 20190729
+
+    def step(k):
+        s0 = (k * world + rank) * S
+        msg.msg_normals(seed, s0, S, M, xi)
+        msg.sample_field(prep, npts, M, gemm, xi, Z)
+        msg.msg_solve_batch(PQ, prm, Z, Qout, status, cycles, relres, ws)
+        msg.mimc_differences(Lidx, p0, q0, Qout, dQ, ptau=ptau, Y=Y)
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    for k in range(a.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    if dist:
+        tdist.barrier()
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    msg.msg_profile_enable(True)
+    launches0 = msg.msg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    conv = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for k in range(a.steps):
+            step(a.warmup + k)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = msg.msg_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    prof = {c: msg.msg_profile_read(c) for c in msg.KERNEL_CLASSES}
+    msg.msg_profile_enable(False)
+    st_last = status.cpu().numpy()
+    conv_frac = float((st_last == 0).mean())
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * S * a.steps * conv_frac / elapsed
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    pin_pq = torch.from_numpy(PQ.copy()).pin_memory()
+    pin_L = torch.from_numpy(Lidx.copy()).pin_memory()
+    dev_pq = torch.empty_like(pin_pq, device=dev)
+    dev_L = torch.empty_like(pin_L, device=dev)
+    h_Q = torch.empty(nq, dtype=torch.float64).pin_memory()
+    h_dQ = torch.empty(nd, dtype=torch.float64).pin_memory()
+    h_Y = torch.empty(S, dtype=torch.float64).pin_memory()
+    h_st = torch.empty(S, dtype=torch.int32).pin_memory()
+    h2d = pin_pq.numel() * 4 + pin_L.numel() * 4
+    d2h = (nq + nd + S) * 8 + S * 4
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        dev_pq.copy_(pin_pq, non_blocking=True)
+        dev_L.copy_(pin_L, non_blocking=True)
+        step(a.warmup + a.steps + k)
+        h_Q.copy_(Qout, non_blocking=True)
+        h_dQ.copy_(dQ, non_blocking=True)
+        h_Y.copy_(Y, non_blocking=True)
+        h_st.copy_(status, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_conv = float((h_st.numpy() == 0).mean())
+    e2e_val = world * S * a.steps * e2e_conv / e2e_s
+
+    # ---- roofline of the dominant kernel (largest event-timed share)
+    hbm, bf16, peak_src = measured_peaks()
+    dom = max(prof, key=lambda c: prof[c]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    if dom == "KL" and a.gemm == "bf16x3":
+        achieved = d["flops"] / (d["ms"] / 1000) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16}
+    else:
+        achieved = d["bytes"] / (d["ms"] / 1000) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm}
+    roof.update({"kernel": dom, "launches": d["launches"], "avg_launch_ms": per_launch_ms,
+                 "share": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-12),
+                 "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1), "traffic": None,
+                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs / bf16_tflops)"})
+    tr = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr):
+        t = json.load(open(tr)).get(dom)
+        if t and t.get("workload") == f"S{S}P{P}Q{Q}" and t.get("build") == build_id():
+            roof["traffic"] = t["dram_bytes_per_launch"]
+
+    # ---- accuracy check (untimed): two samples of the batch against the oracle
+    check = None
+    if rank == 0 and not a.no_check:
+        check = accuracy_check(a, msg, dev, Phi, sl, seed)
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        v, cores, n, wall = oracle_throughput(a, n_samples=a.cpu_samples or None)
+        cpu = {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} FMSG solves at {1 << P}x{1 << Q}, one per thread ({wall:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * elapsed / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "S_per_gpu": S, "P": P, "Q": Q, "M": M, "eps": a.eps,
+                       "omega": a.omega, "l2": "inputs larger than L2 (Z alone is 8.6 GB per step)",
+                       "converged_fraction": conv_frac},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+            "kernel_profile": {c: {"launches": v["launches"], "ms": round(v["ms"], 3)} for c, v in prof.items()
+                               if v["launches"]},
+            "qoi_check": check,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def build_id():
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1907_12334_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1907_12334_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def accuracy_check(a, msg, dev, Phi, sl, seed):
+    """QoI error of the GPU path vs the FP64 oracle on two samples of the first batch.
+
+    solver: GPU solve of the oracle's own FP64 field (isolates the mixed-precision
+    solver); end_to_end: the timed path's field (xi and KL on the GPU, GEMM mode of
+    the run) against the oracle's FP64 field."""
+    import torch
+
+    import oracle
+
+    P, Q, M = a.P, a.Q, a.M
+    idx = [0, 1]
+    xi_o = np.stack([oracle.normals(seed, i, M) for i in idx])
+    Zo = [oracle.kl_field(Phi, sl, xi_o[k]) for k in range(len(idx))]
+    res = oracle.solve_batch([(P, Q)] * len(idx), Zo, oracle.SolverParams(eps=1e-12, max_cycles=600,
+                                                                            omega=a.omega))
+    Qo = np.stack([r[0].ravel() for r in res])
+    prm = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega,
+                           precision=msg.MSG_PREC_MIXED if a.precision == "mixed" else msg.MSG_PREC_FP64)
+    Qg, st, _, _ = msg.solve(np.array([[P, Q]] * len(idx), dtype=np.int32),
+                             torch.from_numpy(np.concatenate(Zo)).to(dev), prm)
+    solver_err = float(np.max(np.abs(Qg.cpu().numpy().reshape(len(idx), -1) - Qo) / np.abs(Qo)))
+    gemm = {"fp64": msg.MSG_GEMM_FP64, "fp32": msg.MSG_GEMM_FP32, "bf16x3": msg.MSG_GEMM_BF16X3}[a.gemm]
+    npts = Phi.shape[0]
+    prep = torch.empty(msg.kl_prepared_bytes(npts, M, gemm), dtype=torch.uint8, device=dev)
+    msg.kl_prepare(torch.from_numpy(np.ascontiguousarray(Phi)).to(dev), torch.from_numpy(np.array(sl)).to(dev), gemm,
+                   prep)
+    xi = torch.empty((len(idx), M), dtype=torch.float64, device=dev)
+    msg.msg_normals(seed, 0, len(idx), M, xi)
+    Zg = torch.empty((len(idx), npts), dtype=torch.float64, device=dev)
+    msg.sample_field(prep, npts, M, gemm, xi, Zg)
+    Qe, _, _, _ = msg.solve(np.array([[P, Q]] * len(idx), dtype=np.int32), Zg.reshape(-1), prm)
+    e2e_err = float(np.max(np.abs(Qe.cpu().numpy().reshape(len(idx), -1) - Qo) / np.abs(Qo)))
+    return {"samples": idx, "oracle_eps": 1e-12, "solver_max_rel_err": solver_err,
+            "end_to_end_max_rel_err": e2e_err, "status": st.cpu().numpy().tolist()}
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        reference_arm(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    ours(a, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

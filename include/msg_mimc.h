@@ -55,6 +55,10 @@ extern "C" {
 #define MSG_QOI_SUBDOMAIN 2 /* Q2 = mean of u over [1/4,1/2]^2, 2-D trapezoid (NaN if p<2 or q<2) */
 #define MSG_QOI_FLUX 3     /* Q3 = -int_0^1 a(1,y) du/dx(1,y) dy, trapezoid + one-sided difference */
 
+/* coefficient of a coarse grid's face (Sec. 2, direct discretisation) */
+#define MSG_COEF_SERIES 0 /* series (harmonic) mean of the finest-face values the face covers */
+#define MSG_COEF_INJECT 1 /* a = exp(Z) at the coarse face midpoint */
+
 /* KL contraction arithmetic */
 #define MSG_GEMM_FP64 0  /* FP64 products and sums */
 #define MSG_GEMM_BF16X3 1 /* tensor cores: bf16 hi/lo splits, hi*hi + hi*lo + lo*hi, FP32 accumulate */
@@ -71,6 +75,7 @@ typedef struct {
     double omega;       /* damping of the coarse-grid correction */
     int32_t precision;  /* MSG_PREC_* */
     int32_t qoi;        /* MSG_QOI_* */
+    int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */
@@ -108,9 +113,11 @@ int32_t sample_field(const void* prepared, int64_t npts, int32_t M, int32_t mode
 /* Sample i has finest grid (P_i, Q_i) = (PQ[2i], PQ[2i+1]), 1 <= P_i, Q_i    */
 /* <= 12, and its field on the (2^(P_i+1)+1) x (2^(Q_i+1)+1) nodes of        */
 /* G^(P_i+1,Q_i+1), x fastest; fields are packed back to back in sample      */
-/* order.  a = exp(Z) is taken at each grid's face midpoints (x-face         */
-/* (i+1/2, j) of G^(p,q) at field node ((2i+1)2^(P-p), 2j 2^(Q-q)), y-face    */
-/* at (2i 2^(P-p), (2j+1)2^(Q-q))).  The right-hand side is h = 1.           */
+/* order.  The finest grid takes a = exp(Z) at its face midpoints (x-face    */
+/* (i+1/2, j) at field node (2i+1, 2j), y-face (i, j+1/2) at (2i, 2j+1)); a  */
+/* coarser face takes the series mean of the finest faces it covers along the */
+/* flux direction (MSG_COEF_SERIES) or exp(Z) at its own midpoint            */
+/* (MSG_COEF_INJECT).  The right-hand side is h = 1.                          */
 /*                                                                          */
 /* Every grid (p,q) of the sample is solved to ||1 - A u||/||1|| <= eps:      */
 /* diagonals p+q are processed in increasing order (Algorithm 2); a grid     */
@@ -145,6 +152,22 @@ int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, con
 /*   written; ptau [host] double or NULL; Y [device] double [S] or NULL.       */
 int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
                          const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation (no counterpart in the paper).                           */
+/*                                                                          */
+/* msg_launch_count: number of CUDA kernels this library has launched in this */
+/* process.  msg_profile_enable(1) clears the records and starts timing every  */
+/* launch with CUDA events on its own stream (0 stops); msg_profile_read sums, */
+/* for one kernel class, the launches, their event-timed milliseconds and      */
+/* their algorithmic bytes and flops (the compulsory traffic/work per launch   */
+/* as defined in the design notes).  Classes: 0 PRE, 1 POST, 2 LOW (cycle      */
+/* visits above / at-and-below the cut), 3 RESIDUAL, 4 UPDATE, 5 INTERP,        */
+/* 6 QOI, 7 COEFFS, 8 NORMALS, 9 KL, 10 MIMC.  msg_profile_read synchronises    */
+/* the recorded events.                                                      */
+int64_t msg_launch_count(void);
+int32_t msg_profile_enable(int32_t on);
+int32_t msg_profile_read(int32_t kernel_class, int64_t* launches, double* total_ms, double* bytes, double* flops);
 
 /* Description of the last error on this thread ("" if none). */
 const char* msg_last_error(void);

@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "kl_tc.cuh"
+#include "prof.cuh"
 
 namespace msg {
 
@@ -128,7 +129,9 @@ extern "C" int32_t msg_normals(uint64_t seed, uint64_t s0, int64_t S, int32_t M,
     if (!xi) { set_error("msg_normals: xi is NULL"); return MSG_ERR_INVALID; }
     int64_t total = S * ((M + 3) / 4);
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    prof_begin(K_NORMALS, (cudaStream_t)stream);
     k_normals<<<blocks, 256, 0, (cudaStream_t)stream>>>(seed, s0, S, M, xi);
+    prof_end(K_NORMALS, (cudaStream_t)stream, 8.0 * S * M, 0.0);
     MSG_CHECK_LAUNCH();
     return MSG_OK;
 }
@@ -168,7 +171,9 @@ extern "C" int32_t kl_prepare(const double* Phi, const double* sqrt_lambda, int6
         MSG_CUDA_TRY(cudaMemcpyAsync(base + align256(sizeof(double) * npts * M), sqrt_lambda, sizeof(double) * M,
                                      cudaMemcpyDeviceToDevice, st));
     } else {
+        prof_begin(K_KL, st);
         k_to_float<<<152 * 8, 256, 0, st>>>(Phi, (float*)base, npts * M);
+        prof_end(K_KL, st, 12.0 * npts * M, 0.0);
         MSG_CHECK_LAUNCH();
         MSG_CUDA_TRY(cudaMemcpyAsync(base + align256(sizeof(float) * npts * M), sqrt_lambda, sizeof(double) * M,
                                      cudaMemcpyDeviceToDevice, st));
@@ -188,6 +193,8 @@ extern "C" int32_t sample_field(const void* prepared, int64_t npts, int32_t M, i
     if (S > 65535LL * 64) { set_error("sample_field: too many samples for one call"); return MSG_ERR_INVALID; }
     dim3 grid((unsigned)((npts + 63) / 64), (unsigned)((S + 63) / 64));
     const char* base = (const char*)prepared;
+    const double pe = mode == MSG_GEMM_FP64 ? 8.0 : 4.0, ze = z_fp32 ? 4.0 : 8.0;
+    prof_begin(K_KL, st);
     if (mode == MSG_GEMM_FP64) {
         const double* Phi = (const double*)base;
         const double* sl = (const double*)(base + align256(sizeof(double) * npts * M));
@@ -202,6 +209,7 @@ extern "C" int32_t sample_field(const void* prepared, int64_t npts, int32_t M, i
         set_error("sample_field: unknown mode");
         return MSG_ERR_INVALID;
     }
+    prof_end(K_KL, st, pe * npts * M + 8.0 * S * M + ze * S * npts, 2.0 * npts * M * S);
     MSG_CHECK_LAUNCH();
     return MSG_OK;
 }

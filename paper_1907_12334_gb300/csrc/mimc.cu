@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace msg {
 
@@ -80,7 +81,9 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
         MSG_CUDA_TRY(cudaMemcpyAsync(dp, ptau, pb, cudaMemcpyHostToDevice, st));
     }
     int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
+    prof_begin(K_MIMC, st);
     k_mimc<<<blocks, 256, 0, st>>>((const MimcSample*)dbuf, S, p0, q0, Q, dp, ld2, dQ, Y);
+    prof_end(K_MIMC, st, 8.0 * (qo + 2.0 * dof) + tb, 0.0);
     MSG_CHECK_LAUNCH();
     MSG_CUDA_TRY(cudaFreeAsync(dbuf, st));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host tables above must outlive the copies

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace msg {
 
@@ -47,23 +48,27 @@ struct SampleInfo {
 // [blk_start[i], blk_start[i] + count of its group) and each of those blocks
 // is one sample of the group.
 struct Segment {
-    int g;          // shape group
-    int pi, qi;     // item (top) grid
-    int p, q;       // task grid (equal to the item grid for item-level lists)
-    int64_t blk_start;
-    int64_t scr_slot; // offset of the item's hierarchy inside the sample's stage scratch
+    int g;              // shape group
+    int pi, qi;         // item (top) grid
+    int p, q;           // task grid (equal to the item grid for item-level lists)
+    int64_t blk_start;  // first block of this segment in its launch
+    int64_t count;      // blocks (samples) in this segment
+    int64_t list_off;   // the segment's samples are slist[list_off .. list_off+count)
+    int64_t scr_slot;   // offset of the item's hierarchy inside the sample's stage scratch
+    int64_t stage_base; // item-level lists: index of (group, item) in the stage's flag array
 };
 
 struct Group {
     int P, Q;
-    int start, count;  // range in perm[]
-    int64_t scr_start; // start of the group's stage scratch (per stage, set when the stage runs)
-    int64_t scr_per_sample;
+    int start, count;       // range of the group's samples in perm[]
+    int64_t scr_start;      // start of the group's stage scratch
+    int64_t scr_per_sample; // stage scratch per sample of the group
 };
 
 struct DevCtx {
     const SampleInfo* samples;
-    const int* perm;
+    const int* gpos;    // position of each sample inside its group
+    const int* slist;   // sample lists the segments index into
     const Group* groups;
     const Segment* segs;
     int nseg;
@@ -85,6 +90,7 @@ struct TaskRef {
     const Segment* seg;
     int64_t scr;    // item hierarchy scratch base
     int64_t item;   // global item id (packed like Qout)
+    int64_t sidx;   // index in the stage's flag array (item-level lists)
 };
 
 __device__ __forceinline__ TaskRef resolve(const DevCtx& cx)
@@ -93,13 +99,14 @@ __device__ __forceinline__ TaskRef resolve(const DevCtx& cx)
     int si = find_segment(cx.segs, cx.nseg, b);
     const Segment* sg = &cx.segs[si];
     const Group& G = cx.groups[sg->g];
-    int local = (int)(b - sg->blk_start);
     TaskRef t;
-    t.s = cx.perm[G.start + local];
+    t.s = cx.slist[sg->list_off + (b - sg->blk_start)];
     t.seg = sg;
-    t.scr = G.scr_start + (int64_t)local * G.scr_per_sample + sg->scr_slot;
+    const int gp = cx.gpos[t.s];
+    t.scr = G.scr_start + (int64_t)gp * G.scr_per_sample + sg->scr_slot;
     const SampleInfo& S = cx.samples[t.s];
     t.item = S.q_off + (int64_t)(sg->pi - 1) * S.Q + (sg->qi - 1);
+    t.sidx = sg->stage_base + gp;
     return t;
 }
 
@@ -349,38 +356,38 @@ __device__ __forceinline__ Hier<T> hier_of(const DevCtx& cx, const TaskRef& t, T
 }
 
 template <class T>
-__global__ void k_pre(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init,
-                      int nu1)
+__global__ void k_pre(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
 {
     TaskRef t = resolve(cx);
-    if (!active[t.item]) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
     visit_pre(h, t.seg->p, t.seg->q, zero_init, nu1);
 }
 
 template <class T>
-__global__ void k_post(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2,
-                       double omega)
+__global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2, double omega)
 {
     TaskRef t = resolve(cx);
-    if (!active[t.item]) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
     visit_post(h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
 template <class T>
-__global__ void k_low(DevCtx cx, const int* active, T* su, T* sbx, T* sby, const T* ax, const T* ay, int d,
-                      int calls, int zero_init, CycleParams cp)
+__global__ void k_low(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int d, int calls, int zero_init,
+                      CycleParams cp)
 {
     TaskRef t = resolve(cx);
-    if (!active[t.item]) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
     for (int c = 0; c < calls; ++c) cta_mu_cycle(h, d, c == 0 ? zero_init : 0, cp);
 }
 
-// Coefficients on every grid: a = exp(Z) at face midpoints (field node of
-// G^(P+1,Q+1) given in the header), scaled by 1/dx^2 and 1/dy^2.
-__global__ void k_coeffs(DevCtx cx, const double* Z, double* ax64, double* ay64, float* ax32, float* ay32)
+// Coefficients on every grid (Sec. 2, direct discretisation on each grid).
+// The finest grid takes a = exp(Z) at its face midpoints (field node
+// (2i+1, 2j) for the x-face (i+1/2, j), (2i, 2j+1) for the y-face).  A coarser
+// face covers sx = 2^(P-p) finest x-faces (sy finest y-faces): coef == 0 takes
+// the series (harmonic) mean of their values along the flux direction,
+// a = sx / sum_k exp(-Z_k); coef == 1 injects exp(Z) at the coarse face
+// midpoint.  Stored scaled by 1/dx^2 and 1/dy^2 (exact: powers of two).
+__global__ void k_coeffs(DevCtx cx, const double* Z, int coef, double* ax64, double* ay64, float* ax32, float* ay32)
 {
     TaskRef t = resolve(cx);
     const SampleInfo& S = cx.samples[t.s];
@@ -393,8 +400,27 @@ __global__ void k_coeffs(DevCtx cx, const double* Z, double* ax64, double* ay64,
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         int i = k % W, j = k / W;
         double vx = 0.0, vy = 0.0;
-        if (i < nx) vx = exp(Zs[(int64_t)(2 * j * sy) * NFx + (2 * i + 1) * sx]) * idx2;
-        if (j < ny) vy = exp(Zs[(int64_t)((2 * j + 1) * sy) * NFx + 2 * i * sx]) * idy2;
+        if (i < nx) {
+            const int64_t row = (int64_t)(2 * j * sy) * NFx;
+            if (coef == 1 || sx == 1) {
+                vx = exp(Zs[row + (2 * i + 1) * sx]);
+            } else {
+                double s = 0.0;
+                for (int m = 0; m < sx; ++m) s += exp(-Zs[row + 2 * (i * sx + m) + 1]);
+                vx = sx / s;
+            }
+            vx *= idx2;
+        }
+        if (j < ny) {
+            if (coef == 1 || sy == 1) {
+                vy = exp(Zs[(int64_t)((2 * j + 1) * sy) * NFx + 2 * i * sx]);
+            } else {
+                double s = 0.0;
+                for (int m = 0; m < sy; ++m) s += exp(-Zs[(int64_t)(2 * (j * sy + m) + 1) * NFx + 2 * i * sx]);
+                vy = sy / s;
+            }
+            vy *= idy2;
+        }
         ax64[off + k] = vx;
         ay64[off + k] = vy;
         if (ax32) {
@@ -470,7 +496,7 @@ __device__ double block_sum(double v)
 // side of the next correction cycle (written into the item's scratch).
 template <class T>
 __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, const double* ay64, T* sbx, int step,
-                           int max_cycles, double eps, int* active, int* cycles, double* relres, int* status,
+                           int max_cycles, double eps, int* sflag, int* cycles, double* relres, int* status,
                            int* counter)
 {
     TaskRef t = resolve(cx);
@@ -481,7 +507,6 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
     const double* ax = ax64 + off;
     const double* ay = ay64 + off;
     T* rb = sbx + t.scr + grid_offset(p, q, q);
-    if (step > 0 && !active[t.item]) return;  // finished earlier
     const int n = (nx - 1) * (ny - 1);
     double acc = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -502,7 +527,7 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
         else if (rr <= eps) act = 0;
         else if (step >= max_cycles) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED); }
         else act = 1;
-        active[t.item] = act;
+        sflag[t.sidx] = act;
         if (!act) {
             cycles[t.item] = step;
             relres[t.item] = rr;
@@ -513,10 +538,9 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
 }
 
 template <class T>
-__global__ void k_update(DevCtx cx, double* u64, const T* su, const int* active)
+__global__ void k_update(DevCtx cx, double* u64, const T* su)
 {
     TaskRef t = resolve(cx);
-    if (!active[t.item]) return;
     const SampleInfo& S = cx.samples[t.s];
     const int p = t.seg->pi, q = t.seg->qi, nx = 1 << p, ny = 1 << q, W = nx + 1;
     double* u = u64 + S.node_off + grid_offset(p, q, S.Q);
@@ -579,26 +603,34 @@ __global__ void k_qoi(DevCtx cx, const double* u64, const double* Z, int qoi, do
 namespace {
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+double pts(int p, int q) { return (double)((1 << p) - 1) * (double)((1 << q) - 1); }
+
+// An item type of a stage: grid (pi, qi) of shape group g.
+struct ItemType {
+    int g, pi, qi;
+    int64_t scr_slot;    // offset of its hierarchy in the sample's stage scratch
+    int64_t stage_base;  // first flag index of this type in the stage's flag array
+};
 
 struct Plan {
     int S = 0;
     std::vector<SampleInfo> samples;
-    std::vector<int> perm;
-    std::vector<Group> groups;  // scr_start / scr_per_sample are per stage (see stage_groups)
+    std::vector<int> perm;  // samples ordered by group
+    std::vector<int> gpos;  // position of each sample inside its group
+    std::vector<Group> groups;
     int Lmax = -1;
-    // per stage L: group tables with the stage's scratch layout
-    std::vector<std::vector<Group>> stage_groups;
-    // segment lists: coefficient/qoi over all grids; per (L, d) task lists; per L item lists
-    std::vector<Segment> all_segs;  // (g, pi=p, qi=q, p, q) over all grids
-    std::vector<std::vector<std::vector<Segment>>> task_segs;  // [L][d]
+    std::vector<std::vector<Group>> stage_groups;   // [L]: groups with the stage's scratch layout
+    std::vector<std::vector<ItemType>> stage_items; // [L]
+    std::vector<int64_t> stage_nitems;              // [L]: flags (items) of the stage
+    std::vector<Segment> all_segs;                  // one segment per grid type over all samples
     int64_t total_nodes = 0, total_field = 0, total_q = 0, scratch_nodes = 0;
-    // device offsets of each segment list in the table area
-    size_t table_bytes = 0;
+    int64_t max_stage_items = 0, max_segs = 0;
 };
 
 int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
 {
     if (S < 0) { set_error("S < 0"); return MSG_ERR_INVALID; }
+    if (S > (int64_t)1 << 30) { set_error("S too large"); return MSG_ERR_INVALID; }
     if (S > 0 && !PQ) { set_error("PQ is NULL"); return MSG_ERR_INVALID; }
     if (!prm) { set_error("params is NULL"); return MSG_ERR_INVALID; }
     if (prm->mu < 1 || prm->mu > 3 || prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 ||
@@ -611,6 +643,10 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         return MSG_ERR_INVALID;
     }
     if (prm->qoi < 0 || prm->qoi > 3) { set_error("qoi out of range"); return MSG_ERR_INVALID; }
+    if (prm->coef != MSG_COEF_SERIES && prm->coef != MSG_COEF_INJECT) {
+        set_error("coef must be MSG_COEF_SERIES or MSG_COEF_INJECT");
+        return MSG_ERR_INVALID;
+    }
     for (int64_t i = 0; i < S; ++i) {
         if (PQ[2 * i] < 1 || PQ[2 * i] > 12 || PQ[2 * i + 1] < 1 || PQ[2 * i + 1] > 12) {
             set_error("grid exponents must satisfy 1 <= P, Q <= 12");
@@ -642,7 +678,8 @@ void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
             int g = (int)pl.groups.size();
             gid[key] = g;
             Group G{};
-            G.P = si.P; G.Q = si.Q;
+            G.P = si.P;
+            G.Q = si.Q;
             pl.groups.push_back(G);
             sample_group[i] = g;
         } else {
@@ -650,7 +687,6 @@ void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
         }
         pl.Lmax = std::max(pl.Lmax, si.P + si.Q - 2);
     }
-    // perm: samples ordered by group
     std::vector<int> cnt(pl.groups.size(), 0);
     for (int64_t i = 0; i < S; ++i) cnt[sample_group[i]]++;
     int acc = 0;
@@ -661,62 +697,50 @@ void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
         cnt[g] = pl.groups[g].start;
     }
     pl.perm.resize(S);
-    for (int64_t i = 0; i < S; ++i) pl.perm[cnt[sample_group[i]]++] = (int)i;
-
-    // all-grid segments (coefficients)
+    pl.gpos.resize(S);
+    for (int64_t i = 0; i < S; ++i) {
+        int g = sample_group[i];
+        pl.gpos[i] = cnt[g] - pl.groups[g].start;
+        pl.perm[cnt[g]++] = (int)i;
+    }
     int64_t blk = 0;
     for (size_t g = 0; g < pl.groups.size(); ++g)
         for (int p = 1; p <= pl.groups[g].P; ++p)
             for (int q = 1; q <= pl.groups[g].Q; ++q) {
-                Segment sg{(int)g, p, q, p, q, blk, 0};
+                Segment sg{(int)g, p, q, p, q, blk, pl.groups[g].count, pl.groups[g].start, 0, 0};
                 pl.all_segs.push_back(sg);
                 blk += pl.groups[g].count;
             }
-
-    // stages
     pl.stage_groups.assign(pl.Lmax + 1, pl.groups);
-    pl.task_segs.assign(pl.Lmax + 1, {});
+    pl.stage_items.assign(pl.Lmax + 1, {});
+    pl.stage_nitems.assign(pl.Lmax + 1, 0);
     for (int L = 0; L <= pl.Lmax; ++L) {
         std::vector<Group>& sg = pl.stage_groups[L];
-        int64_t scr = 0;
-        std::vector<std::vector<int64_t>> slot(pl.groups.size());
+        int64_t scr = 0, base = 0, nseg = 0;
         for (size_t g = 0; g < sg.size(); ++g) {
             int64_t per = 0;
             for (int p = 1; p <= sg[g].P; ++p) {
                 int q = L + 2 - p;
                 if (q < 1 || q > sg[g].Q) continue;
-                slot[g].push_back(per);
+                pl.stage_items[L].push_back(ItemType{(int)g, p, q, per, base});
                 per += rect_nodes(p, q);
+                base += sg[g].count;
+                nseg += (int64_t)p * q;  // tasks of all diagonals of this item's hierarchy
             }
             sg[g].scr_start = scr;
             sg[g].scr_per_sample = per;
             scr += per * sg[g].count;
         }
+        pl.stage_nitems[L] = base;
         pl.scratch_nodes = std::max(pl.scratch_nodes, scr);
-        pl.task_segs[L].assign(L + 1, {});
-        for (int d = 0; d <= L; ++d) {
-            int64_t b = 0;
-            std::vector<Segment>& v = pl.task_segs[L][d];
-            for (size_t g = 0; g < sg.size(); ++g) {
-                int k = 0;
-                for (int pi = 1; pi <= sg[g].P; ++pi) {
-                    int qi = L + 2 - pi;
-                    if (qi < 1 || qi > sg[g].Q) continue;
-                    for (int p = std::max(1, d + 2 - qi); p <= std::min(pi, d + 1); ++p) {
-                        Segment s{(int)g, pi, qi, p, d + 2 - p, b, slot[g][k]};
-                        v.push_back(s);
-                        b += sg[g].count;
-                    }
-                    ++k;
-                }
-            }
-        }
+        pl.max_stage_items = std::max(pl.max_stage_items, base);
+        pl.max_segs = std::max(pl.max_segs, nseg + (int64_t)pl.stage_items[L].size());
     }
 }
 
 struct WsLayout {
-    size_t samples, perm, groups, segs, nsegs_total;
-    size_t active, cycles_i, relres_i, counter;
+    size_t samples, perm, gpos, groups, allsegs, stepsegs, slist, sflag;
+    size_t cycles_i, relres_i, counter;
     size_t u64, ax64, ay64, ax32, ay32, su, sbx, sby;
     size_t total;
 };
@@ -725,18 +749,17 @@ WsLayout layout_of(const Plan& pl, int precision)
 {
     WsLayout w{};
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-    size_t nseg = pl.all_segs.size();
-    for (int L = 0; L <= pl.Lmax; ++L)
-        for (int d = 0; d <= L; ++d) nseg += pl.task_segs[L][d].size();
-    w.nsegs_total = nseg;
-    w.samples = take(sizeof(SampleInfo) * std::max<int64_t>(pl.S, 1));
-    w.perm = take(sizeof(int) * std::max<int64_t>(pl.S, 1));
-    w.groups = take(sizeof(Group) * std::max<size_t>(1, pl.groups.size() * (pl.Lmax + 2)));
-    w.segs = take(sizeof(Segment) * std::max<size_t>(nseg, 1));
-    w.active = take(sizeof(int) * std::max<int64_t>(pl.total_q, 1));
-    w.cycles_i = take(sizeof(int) * std::max<int64_t>(pl.total_q, 1));
-    w.relres_i = take(sizeof(double) * std::max<int64_t>(pl.total_q, 1));
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
+    w.samples = take(sizeof(SampleInfo) * pl.S);
+    w.perm = take(sizeof(int) * pl.S);
+    w.gpos = take(sizeof(int) * pl.S);
+    w.groups = take(sizeof(Group) * pl.groups.size() * (pl.Lmax + 2));
+    w.allsegs = take(sizeof(Segment) * pl.all_segs.size());
+    w.stepsegs = take(sizeof(Segment) * pl.max_segs);
+    w.slist = take(sizeof(int) * pl.max_stage_items);
+    w.sflag = take(sizeof(int) * pl.max_stage_items);
+    w.cycles_i = take(sizeof(int) * pl.total_q);
+    w.relres_i = take(sizeof(double) * pl.total_q);
     w.counter = take(sizeof(int) * 4);
     w.u64 = take(sizeof(double) * pl.total_nodes);
     w.ax64 = take(sizeof(double) * pl.total_nodes);
@@ -753,33 +776,19 @@ WsLayout layout_of(const Plan& pl, int precision)
     return w;
 }
 
-int lowcut(int precision) { return precision == MSG_PREC_MIXED ? 6 : 6; }
-
 constexpr int kThreads = 256;
+constexpr int kLowCut = 6;  // diagonals <= kLowCut of a hierarchy run inside one launch per item
 
-template <class T>
-struct Runner {
-    const Plan& pl;
-    const WsLayout& wl;
-    char* ws;
-    cudaStream_t st;
-    const msg_params& prm;
-    DevCtx base;            // samples, perm filled in
-    const Group* dgroups;   // device stage group tables
-    const Segment* dsegs;   // device segments
-    std::vector<size_t> seg_index;  // start index of each list in dsegs
-    T* su; T* sbx; T* sby;
-    const T* ax; const T* ay;
-    int* active;
-    CycleParams cp;
-
-    DevCtx ctx(const Group* groups, const Segment* segs, int nseg) const
+// Host staging for the per-step lists (pinned so the uploads are asynchronous).
+struct Pinned {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~Pinned() { if (p) cudaFreeHost(p); }
+    int alloc(size_t b)
     {
-        DevCtx c = base;
-        c.groups = groups;
-        c.segs = segs;
-        c.nseg = nseg;
-        return c;
+        if (cudaMallocHost(&p, std::max<size_t>(b, 64)) != cudaSuccess) { p = nullptr; return MSG_ERR_CUDA; }
+        bytes = b;
+        return MSG_OK;
     }
 };
 
@@ -789,31 +798,21 @@ struct Runner {
 
 template <class T>
 static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_params& prm, const double* Z,
-                     double* Qout, int32_t* status, int32_t* cycles_out, double* relres_out, cudaStream_t st)
+                     double* Qout, int32_t* stat, int32_t* cycles_out, double* relres_out, cudaStream_t st)
 {
-    // ---- upload tables
-    std::vector<Segment> segs;
-    std::vector<size_t> all_idx(1, 0);
-    segs.insert(segs.end(), pl.all_segs.begin(), pl.all_segs.end());
-    std::vector<std::vector<size_t>> tidx(pl.Lmax + 1);
-    for (int L = 0; L <= pl.Lmax; ++L) {
-        tidx[L].resize(L + 1);
-        for (int d = 0; d <= L; ++d) {
-            tidx[L][d] = segs.size();
-            segs.insert(segs.end(), pl.task_segs[L][d].begin(), pl.task_segs[L][d].end());
-        }
-    }
-    std::vector<Group> gtab;  // [0]: plain groups, [1+L]: stage L groups
+    const bool mixed = prm.precision == MSG_PREC_MIXED;
+    const size_t ng = pl.groups.size();
+    // ---- static tables
+    std::vector<Group> gtab;  // [0]: groups, [1+L]: stage L groups
     gtab.insert(gtab.end(), pl.groups.begin(), pl.groups.end());
     for (int L = 0; L <= pl.Lmax; ++L) gtab.insert(gtab.end(), pl.stage_groups[L].begin(), pl.stage_groups[L].end());
-    const size_t ng = pl.groups.size();
-
     MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.samples, pl.samples.data(), sizeof(SampleInfo) * pl.S, cudaMemcpyHostToDevice, st));
     MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.perm, pl.perm.data(), sizeof(int) * pl.S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.gpos, pl.gpos.data(), sizeof(int) * pl.S, cudaMemcpyHostToDevice, st));
     MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.groups, gtab.data(), sizeof(Group) * gtab.size(), cudaMemcpyHostToDevice, st));
-    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.segs, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.allsegs, pl.all_segs.data(), sizeof(Segment) * pl.all_segs.size(),
+                                 cudaMemcpyHostToDevice, st));
 
-    const bool mixed = prm.precision == MSG_PREC_MIXED;
     double* u64 = (double*)(ws + wl.u64);
     double* ax64 = (double*)(ws + wl.ax64);
     double* ay64 = (double*)(ws + wl.ay64);
@@ -824,103 +823,206 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     T* sby = (T*)(ws + wl.sby);
     const T* ax = mixed ? (const T*)ax32 : (const T*)ax64;
     const T* ay = mixed ? (const T*)ay32 : (const T*)ay64;
-    int* active = (int*)(ws + wl.active);
     int* cyc = (int*)(ws + wl.cycles_i);
     double* rel = (double*)(ws + wl.relres_i);
     int* counter = (int*)(ws + wl.counter);
-    const Segment* dsegs = (const Segment*)(ws + wl.segs);
+    int* sflag = (int*)(ws + wl.sflag);
+    int* slist = (int*)(ws + wl.slist);
+    Segment* stepsegs = (Segment*)(ws + wl.stepsegs);
     const Group* dgroups = (const Group*)(ws + wl.groups);
 
-    // per-sample status: caller's array or a private copy
-    int32_t* stat = status;
-    std::vector<int32_t> zero_status;
-    if (!stat) return (set_error("internal: status buffer missing"), MSG_ERR_INVALID);
     MSG_CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(int32_t) * pl.S, st));
     MSG_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * pl.total_nodes, st));
-    MSG_CUDA_TRY(cudaMemsetAsync(su, 0, sizeof(T) * pl.scratch_nodes, st));
-    MSG_CUDA_TRY(cudaMemsetAsync(active, 0, sizeof(int) * std::max<int64_t>(pl.total_q, 1), st));
 
     DevCtx base{};
     base.samples = (const SampleInfo*)(ws + wl.samples);
-    base.perm = (const int*)(ws + wl.perm);
-    auto ctx = [&](const Group* g, size_t seg0, size_t n) {
-        DevCtx c = base;
-        c.groups = g;
-        c.segs = dsegs + seg0;
-        c.nseg = (int)n;
-        return c;
-    };
-    auto nblocks = [&](const std::vector<Segment>& v, const std::vector<Group>& gt) -> int64_t {
-        if (v.empty()) return 0;
-        return v.back().blk_start + gt[v.back().g].count;
-    };
+    base.gpos = (const int*)(ws + wl.gpos);
 
-    // coefficients on every grid
+    // ---- coefficients on every grid
     {
-        int64_t nb = nblocks(pl.all_segs, pl.groups);
-        if (nb > 0) {
-            k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(ctx(dgroups, 0, pl.all_segs.size()), Z, ax64, ay64, ax32, ay32);
-            MSG_CHECK_LAUNCH();
-        }
+        DevCtx c = base;
+        c.slist = (const int*)(ws + wl.perm);
+        c.groups = dgroups;
+        c.segs = (const Segment*)(ws + wl.allsegs);
+        c.nseg = (int)pl.all_segs.size();
+        int64_t nb = pl.all_segs.empty() ? 0 : pl.all_segs.back().blk_start + pl.all_segs.back().count;
+        double nodes = 0;
+        for (const Segment& s : pl.all_segs) nodes += (double)s.count * ((1 << s.p) + 1) * ((1 << s.q) + 1);
+        prof_begin(K_COEFFS, st);
+        k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(c, Z, prm.coef, ax64, ay64, ax32, ay32);
+        prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
+        MSG_CHECK_LAUNCH();
     }
 
-    const int dcut = lowcut(prm.precision);
-    CycleParams cp{prm.mu, prm.nu1, prm.nu2, prm.omega};
-    int* hcount = nullptr;
-    MSG_CUDA_TRY(cudaMallocHost(&hcount, sizeof(int)));  // pinned flag readback
-    struct PinnedFree { int* p; ~PinnedFree() { if (p) cudaFreeHost(p); } } pf{hcount};
+    // ---- host staging for the per-step lists: [counter | flags | sample list | segments]
+    const size_t flag_bytes = sizeof(int) * std::max<int64_t>(pl.max_stage_items, 1);
+    const size_t list_bytes = flag_bytes;
+    const size_t seg_bytes = sizeof(Segment) * std::max<int64_t>(pl.max_segs, 1);
+    Pinned pin;
+    if (pin.alloc(64 + flag_bytes + list_bytes + seg_bytes) != MSG_OK) {
+        set_error("cudaMallocHost failed");
+        return MSG_ERR_CUDA;
+    }
+    int* h_counter = (int*)pin.p;
+    int* h_flags = (int*)((char*)pin.p + 64);
+    int* h_list = (int*)((char*)pin.p + 64 + flag_bytes);
+    Segment* h_segs = (Segment*)((char*)pin.p + 64 + flag_bytes + list_bytes);
+
+    const CycleParams cp{prm.mu, prm.nu1, prm.nu2, prm.omega};
+    const double es = sizeof(T);
 
     for (int L = 0; L <= pl.Lmax; ++L) {
-        const Group* sg = dgroups + ng * (1 + L);
+        const std::vector<ItemType>& its = pl.stage_items[L];
+        if (its.empty()) continue;
         const std::vector<Group>& hsg = pl.stage_groups[L];
-        const std::vector<Segment>& items = pl.task_segs[L][L];
-        int64_t nit = nblocks(items, hsg);
-        if (nit == 0) continue;
-        DevCtx ic = ctx(sg, tidx[L][L], items.size());
-        k_interp<<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, ax64, ay64);
-        MSG_CHECK_LAUNCH();
-        for (int step = 0;; ++step) {
-            MSG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-            k_residual<T><<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, ax64, ay64, sbx, step, prm.max_cycles, prm.eps,
-                                                             active, cyc, rel, stat, counter);
+        const Group* sg = dgroups + ng * (1 + L);
+        // Per-step segment lists (device copy in stepsegs): item-level list, then one
+        // list per diagonal d in (kLowCut, L].  `active` holds, per item type, the
+        // group positions of the samples whose item is still iterating.
+        std::vector<std::vector<int>> active(its.size());
+        for (size_t k = 0; k < its.size(); ++k) {
+            const Group& G = hsg[its[k].g];
+            active[k].resize(G.count);
+            for (int i = 0; i < G.count; ++i) active[k][i] = pl.perm[G.start + i];
+        }
+        size_t item_seg0 = 0, item_nseg = 0;
+        std::vector<size_t> dseg0(L + 1, 0), dnseg(L + 1, 0);
+        std::vector<double> dpts_pre(L + 1, 0), dpts_post(L + 1, 0);
+        int64_t nitems_active = 0;
+        double item_pts = 0, low_bytes = 0;
+        auto build_lists = [&]() {
+            // sample list
+            std::vector<int64_t> loff(its.size());
+            int64_t nl = 0;
+            item_pts = 0;
+            for (size_t k = 0; k < its.size(); ++k) {
+                loff[k] = nl;
+                for (int s : active[k]) h_list[nl++] = s;
+                item_pts += (double)active[k].size() * pts(its[k].pi, its[k].qi);
+            }
+            nitems_active = nl;
+            size_t ns = 0;
+            int64_t b = 0;
+            item_seg0 = 0;
+            for (size_t k = 0; k < its.size(); ++k) {
+                if (active[k].empty()) continue;
+                const ItemType& it = its[k];
+                h_segs[ns++] = Segment{it.g, it.pi, it.qi, it.pi, it.qi, b, (int64_t)active[k].size(), loff[k],
+                                       it.scr_slot, it.stage_base};
+                b += (int64_t)active[k].size();
+            }
+            item_nseg = ns;
+            // algorithmic bytes of one LOW launch at diagonal min(L, kLowCut)
+            const int dl = std::min(L, kLowCut);
+            low_bytes = 0;
+            for (size_t k = 0; k < its.size(); ++k)
+                for (int pp = 1; pp <= its[k].pi; ++pp)
+                    for (int qq = 1; qq <= its[k].qi; ++qq) {
+                        int dd = pp + qq - 2;
+                        if (dd > dl) continue;
+                        double n = (double)active[k].size() * pts(pp, qq);
+                        low_bytes += n * 2;
+                        if (dd == dl) low_bytes += n * ((pp < its[k].pi && qq < its[k].qi) ? 3 : 2);
+                    }
+            low_bytes *= es;
+            for (int d = kLowCut + 1; d <= L; ++d) {
+                dseg0[d] = ns;
+                b = 0;
+                dpts_pre[d] = dpts_post[d] = 0;
+                for (size_t k = 0; k < its.size(); ++k) {
+                    if (active[k].empty()) continue;
+                    const ItemType& it = its[k];
+                    for (int p = std::max(1, d + 2 - it.qi); p <= std::min(it.pi, d + 1); ++p) {
+                        const int q = d + 2 - p;
+                        h_segs[ns++] = Segment{it.g, it.pi, it.qi, p, q, b, (int64_t)active[k].size(), loff[k],
+                                               it.scr_slot, it.stage_base};
+                        b += (int64_t)active[k].size();
+                        const double n = (double)active[k].size() * pts(p, q);
+                        const double bw = (p < it.pi && q < it.qi) ? 2.0 : 1.0;
+                        const double ch = (p > 1 ? 0.5 : 0.0) + (q > 1 ? 0.5 : 0.0);
+                        dpts_pre[d] += n * (bw + 2 + 1 + ch);  // b, coefficients, u out, restriction out
+                        dpts_post[d] += n * (ch + bw + 2 + 2); // children, b, coefficients, u in/out
+                    }
+                }
+                dnseg[d] = ns - dseg0[d];
+            }
+            MSG_CUDA_TRY(cudaMemcpyAsync(slist, h_list, sizeof(int) * std::max<int64_t>(nl, 1), cudaMemcpyHostToDevice, st));
+            MSG_CUDA_TRY(cudaMemcpyAsync(stepsegs, h_segs, sizeof(Segment) * std::max<size_t>(ns, 1),
+                                         cudaMemcpyHostToDevice, st));
+            return MSG_OK;
+        };
+        auto ctx_of = [&](size_t seg0, size_t n) {
+            DevCtx c = base;
+            c.slist = slist;
+            c.groups = sg;
+            c.segs = stepsegs + seg0;
+            c.nseg = (int)n;
+            return c;
+        };
+        int rc = build_lists();
+        if (rc != MSG_OK) return rc;
+        DevCtx all_items = ctx_of(item_seg0, item_nseg);
+        const int64_t nall = nitems_active;
+        {
+            prof_begin(K_INTERP, st);
+            k_interp<<<(unsigned)nall, kThreads, 0, st>>>(all_items, u64, ax64, ay64);
+            prof_end(K_INTERP, st, item_pts * (8.0 + 16.0 + 8.0), 0.0);
             MSG_CHECK_LAUNCH();
-            MSG_CUDA_TRY(cudaMemcpyAsync(hcount, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        for (int step = 0;; ++step) {
+            DevCtx ic = ctx_of(item_seg0, item_nseg);
+            MSG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+            prof_begin(K_RESIDUAL, st);
+            k_residual<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, u64, ax64, ay64, sbx, step, prm.max_cycles,
+                                                                       prm.eps, sflag, cyc, rel, stat, counter);
+            prof_end(K_RESIDUAL, st, item_pts * (24.0 + es), 0.0);
+            MSG_CHECK_LAUNCH();
+            MSG_CUDA_TRY(cudaMemcpyAsync(h_counter, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MSG_CUDA_TRY(cudaMemcpyAsync(h_flags, sflag, sizeof(int) * pl.stage_nitems[L], cudaMemcpyDeviceToHost, st));
             MSG_CUDA_TRY(cudaStreamSynchronize(st));
-            if (*hcount == 0) break;
-            // one mu-cycle of every active item: recursive launch schedule
-            struct Emitter {
-                int L, dcut, mu;
-                std::vector<std::pair<int, std::vector<int>>> ops;  // unused
-            };
-            // recursive lambda through std::function-free helper
-            int err = MSG_OK;
+            if (*h_counter == 0) break;
+            // keep the items whose flag is set
+            for (size_t k = 0; k < its.size(); ++k) {
+                std::vector<int>& a = active[k];
+                size_t w = 0;
+                for (size_t r = 0; r < a.size(); ++r)
+                    if (h_flags[its[k].stage_base + pl.gpos[a[r]]]) a[w++] = a[r];
+                a.resize(w);
+            }
+            rc = build_lists();
+            if (rc != MSG_OK) return rc;
+            ic = ctx_of(item_seg0, item_nseg);
+            // one mu-cycle (Algorithm 1) of every active item
+            bool launch_err = false;
             auto launch_low = [&](int d, int calls, int zi) {
-                DevCtx c = ic;
-                k_low<T><<<(unsigned)nit, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, d, calls, zi, cp);
-                if (cudaGetLastError() != cudaSuccess) err = MSG_ERR_CUDA;
+                prof_begin(K_LOW, st);
+                k_low<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, su, sbx, sby, ax, ay, d, calls, zi, cp);
+                prof_end(K_LOW, st, low_bytes, 0.0);
+                launch_err |= cudaGetLastError() != cudaSuccess;
             };
             auto launch_half = [&](int d, int pre, int zi) {
-                const std::vector<Segment>& v = pl.task_segs[L][d];
-                int64_t nb = nblocks(v, hsg);
-                if (nb == 0) return;
-                DevCtx c = ctx(sg, tidx[L][d], v.size());
-                if (pre) k_pre<T><<<(unsigned)nb, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, zi, prm.nu1);
-                else k_post<T><<<(unsigned)nb, kThreads, 0, st>>>(c, active, su, sbx, sby, ax, ay, prm.nu2, prm.omega);
-                if (cudaGetLastError() != cudaSuccess) err = MSG_ERR_CUDA;
+                if (dnseg[d] == 0) return;
+                const Segment& last = h_segs[dseg0[d] + dnseg[d] - 1];
+                const int64_t nb = last.blk_start + last.count;
+                DevCtx c = ctx_of(dseg0[d], dnseg[d]);
+                prof_begin(pre ? K_PRE : K_POST, st);
+                if (pre) k_pre<T><<<(unsigned)nb, kThreads, 0, st>>>(c, su, sbx, sby, ax, ay, zi, prm.nu1);
+                else k_post<T><<<(unsigned)nb, kThreads, 0, st>>>(c, su, sbx, sby, ax, ay, prm.nu2, prm.omega);
+                prof_end(pre ? K_PRE : K_POST, st, (pre ? dpts_pre[d] : dpts_post[d]) * es, 0.0);
+                launch_err |= cudaGetLastError() != cudaSuccess;
             };
-            // iterative emission of the recursion of Algorithm 1 above dcut
-            struct Frame { int d, k, zi, phase; };
-            std::vector<Frame> stack;
-            if (L <= dcut) {
+            if (L <= kLowCut) {
                 launch_low(L, 1, 1);
             } else {
+                struct Frame { int d, k, zi, phase; };
+                std::vector<Frame> stack;
                 stack.push_back({L, 0, 1, 0});
                 while (!stack.empty()) {
                     Frame& f = stack.back();
                     if (f.phase == 0) {
                         launch_half(f.d, 1, f.zi);
                         f.phase = 1;
-                        if (f.d - 1 <= dcut) {
+                        if (f.d - 1 <= kLowCut) {
                             launch_low(f.d - 1, prm.mu, 1);
                             f.phase = 2;
                         }
@@ -939,12 +1041,25 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
                     stack.pop_back();
                 }
             }
-            if (err) { set_error("kernel launch failed in the cycle schedule"); return MSG_ERR_CUDA; }
-            k_update<T><<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, su, active);
+            if (launch_err) { set_error("kernel launch failed in the cycle schedule"); return MSG_ERR_CUDA; }
+            prof_begin(K_UPDATE, st);
+            k_update<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, u64, su);
+            prof_end(K_UPDATE, st, item_pts * (16.0 + es), 0.0);
             MSG_CHECK_LAUNCH();
         }
-        k_qoi<<<(unsigned)nit, kThreads, 0, st>>>(ic, u64, Z, prm.qoi, Qout);
+        // QoI of every item of the stage (all samples)
+        for (size_t k = 0; k < its.size(); ++k) {
+            const Group& G = hsg[its[k].g];
+            active[k].resize(G.count);
+            for (int i = 0; i < G.count; ++i) active[k][i] = pl.perm[G.start + i];
+        }
+        rc = build_lists();
+        if (rc != MSG_OK) return rc;
+        prof_begin(K_QOI, st);
+        k_qoi<<<(unsigned)nitems_active, kThreads, 0, st>>>(ctx_of(item_seg0, item_nseg), u64, Z, prm.qoi, Qout);
+        prof_end(K_QOI, st, item_pts * 8.0, 0.0);
         MSG_CHECK_LAUNCH();
+        MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host lists are rewritten by the next stage
     }
     if (cycles_out) MSG_CUDA_TRY(cudaMemcpyAsync(cycles_out, cyc, sizeof(int) * pl.total_q, cudaMemcpyDeviceToDevice, st));
     if (relres_out) MSG_CUDA_TRY(cudaMemcpyAsync(relres_out, rel, sizeof(double) * pl.total_q, cudaMemcpyDeviceToDevice, st));
@@ -978,20 +1093,14 @@ extern "C" int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_param
     Plan pl;
     build_plan(PQ, S, pl);
     WsLayout wl = layout_of(pl, prm->precision);
-    size_t need = wl.total + align_up(sizeof(int32_t) * S);
+    const size_t need = wl.total + align_up(sizeof(int32_t) * S);
     if (ws_bytes < need) {
         set_error("workspace too small: need " + std::to_string(need) + " bytes");
         return MSG_ERR_WORKSPACE;
     }
-    char* ws = (char*)workspace;
-    ws = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    if ((size_t)(ws - (char*)workspace) + need - 256 > ws_bytes) {
-        set_error("workspace too small after alignment");
-        return MSG_ERR_WORKSPACE;
-    }
+    char* ws = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     int32_t* stat = status ? status : (int32_t*)(ws + wl.total);
     cudaStream_t st = (cudaStream_t)stream;
-    if (prm->precision == MSG_PREC_MIXED)
-        return run_solve<float>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
+    if (prm->precision == MSG_PREC_MIXED) return run_solve<float>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
     return run_solve<double>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
 }

@@ -22,9 +22,12 @@ MSG_SAMPLE_NOT_CONVERGED, MSG_SAMPLE_NONFINITE = 1, 2
 MSG_PREC_FP64, MSG_PREC_MIXED = 0, 1
 MSG_QOI_INTEGRAL, MSG_QOI_POINT, MSG_QOI_SUBDOMAIN, MSG_QOI_FLUX = 0, 1, 2, 3
 MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32 = 0, 1, 2
+MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
-            "msg_solve_batch", "mimc_differences", "msg_last_error", "msg_version")
+            "msg_solve_batch", "mimc_differences", "msg_last_error", "msg_version", "msg_launch_count",
+            "msg_profile_enable", "msg_profile_read")
+KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
 
 
 class MsgError(RuntimeError):
@@ -34,7 +37,7 @@ class MsgError(RuntimeError):
 class msg_params(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32)]
 
 
 @dataclass
@@ -48,10 +51,11 @@ class SolverParams:
     omega: float = 1.0
     precision: int = MSG_PREC_MIXED
     qoi: int = MSG_QOI_INTEGRAL
+    coef: int = MSG_COEF_SERIES
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
-                          self.qoi)
+                          self.qoi, self.coef)
 
 
 _lib = None
@@ -90,6 +94,13 @@ def load(path: str | None = None):
     L.msg_last_error.restype = ctypes.c_char_p
     L.msg_version.argtypes = []
     L.msg_version.restype = ctypes.c_char_p
+    L.msg_launch_count.argtypes = []
+    L.msg_launch_count.restype = i64
+    L.msg_profile_enable.argtypes = [i32]
+    L.msg_profile_enable.restype = i32
+    L.msg_profile_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                   ctypes.POINTER(dbl)]
+    L.msg_profile_read.restype = i32
     _lib = L
     return L
 
@@ -174,6 +185,23 @@ def mimc_differences(L, p0: int, q0: int, Q, dQ, ptau=None, Y=None, stream=None)
 
 def msg_version() -> str:
     return load().msg_version().decode()
+
+
+def msg_launch_count() -> int:
+    return int(load().msg_launch_count())
+
+
+def msg_profile_enable(on: bool):
+    _check(load().msg_profile_enable(1 if on else 0))
+
+
+def msg_profile_read(kernel_class) -> dict:
+    """{launches, ms, bytes, flops} summed over the recorded launches of one class."""
+    k = KERNEL_CLASSES.index(kernel_class) if isinstance(kernel_class, str) else int(kernel_class)
+    n = ctypes.c_int64()
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().msg_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
 
 
 # ------------------------------------------------------------ conveniences --
