@@ -542,7 +542,10 @@ static double grid_relres(ogrid* g)
  * iterated by Algorithm 1 with (p,q) as the finest grid of its own hierarchy
  * {(p',q'): p' <= p, q' <= q} (so the two-parent average only ever combines
  * residuals of one error), until its own ||r||/||b|| <= eps (at least one
- * cycle, at most max_cycles).  The solution of each grid is saved when its
+ * cycle, at most max_cycles).  READING: the paper only says the cycle count is
+ * increased until the criterion holds; a grid whose relative residual after
+ * a cycle exceeds 1 (worse than the zero guess) has diverged and stops there,
+ * flagged as not converged, instead of running on to max_cycles.  The solution of each grid is saved when its
  * stage ends, before cycles on finer diagonals reuse its u and b as scratch. */
 static void f_cycle(ohier* H, int s)
 {
@@ -564,7 +567,7 @@ static void f_cycle(ohier* H, int s)
             orc_mu_cycle(H, s);
             ++n;
             rr = grid_relres(g);
-        } while (!(rr <= H->eps) && n < H->max_cycles && rr == rr);
+        } while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && rr <= 1.0);
         H->Pa = H->P; H->Qa = H->Q;
         H->grid_cycles[(p - 1) * H->Q + (q - 1)] = n;
         H->grid_relres[(p - 1) * H->Q + (q - 1)] = rr;
