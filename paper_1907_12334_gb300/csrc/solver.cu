@@ -12,10 +12,10 @@
 // For a linear cycle this is the same iteration as cycling on (u, 1).
 //
 // Launch structure of one cycle for all active items of a stage: diagonals
-// d > dcut of the items' hierarchies are visited by one launch per visit half
+// d > kDW of the items' hierarchies are visited by one launch per visit half
 // (PRE: zero/smooth nu1/restrict; POST: prolong/smooth nu2) with one CTA per
-// (item, grid) task; everything at or below dcut runs inside one launch
-// (LOW) with one CTA per item walking the recursion of Algorithm 1.
+// (item, grid) task; everything at or below kDW runs inside one launch (LOW)
+// with one warp per item walking the recursion of Algorithm 1 in shared memory.
 //
 // Storage (all node-indexed with the boundary, see common.cuh):
 //   u64          solution of every grid of every sample (FP64)
@@ -93,9 +93,8 @@ struct TaskRef {
     int64_t sidx;   // index in the stage's flag array (item-level lists)
 };
 
-__device__ __forceinline__ TaskRef resolve(const DevCtx& cx)
+__device__ __forceinline__ TaskRef resolve_at(const DevCtx& cx, int64_t b)
 {
-    int64_t b = blockIdx.x;
     int si = find_segment(cx.segs, cx.nseg, b);
     const Segment* sg = &cx.segs[si];
     const Group& G = cx.groups[sg->g];
@@ -110,7 +109,14 @@ __device__ __forceinline__ TaskRef resolve(const DevCtx& cx)
     return t;
 }
 
+__device__ __forceinline__ TaskRef resolve(const DevCtx& cx) { return resolve_at(cx, blockIdx.x); }
+
 // ------------------------------------------------------------ grid ops ----
+
+// 1/x: the correctly rounded FP32 reciprocal in the FP32 cycles (the cycles only
+// produce a correction; the FP64 residual decides convergence), exact in FP64.
+__device__ __forceinline__ float rcp_of(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_of(double x) { return 1.0 / x; }
 
 template <class T>
 struct GView {
@@ -163,7 +169,7 @@ __device__ void cta_smooth(const GView<T>& g, int sweeps)
                 int c = j * W + i;
                 T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
                 T nb = (aw * g.u[c - 1] + ae * g.u[c + 1]) + (as * g.u[c - W] + an * g.u[c + W]);
-                g.u[c] = (b_at(g, c) + nb) / (aw + ae + as + an);
+                g.u[c] = (b_at(g, c) + nb) * rcp_of(aw + ae + as + an);
             }
             __syncthreads();
         }
@@ -228,8 +234,8 @@ __device__ void cta_prolong(const GView<T>& g, const T* ucx, const T* ucy, T ome
         T corr;
         if (ucx && ucy) {
             T cxv = g.ax[c - 1] + g.ax[c], cyv = g.ay[c - W] + g.ay[c];
-            T x2 = cxv * cxv, y2 = cyv * cyv;
-            corr = (x2 / (x2 + y2)) * vx + (y2 / (x2 + y2)) * vy;
+            T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+            corr = (x2 * s) * vx + (y2 * s) * vy;
         } else {
             corr = ucx ? vx : vy;
         }
@@ -306,39 +312,6 @@ __device__ __forceinline__ void diag_range(int d, int pi, int qi, int& plo, int&
     phi = min(pi, d + 1);
 }
 
-// mu-cycle (Algorithm 1) on diagonals <= d of one item's hierarchy, run by one CTA.
-template <class T>
-__device__ void cta_mu_cycle(const Hier<T>& h, int d, int zero_init, const CycleParams& cp)
-{
-    // explicit stack of (d, phase, k, zero_init): phase 0 = PRE, 1 = children, 2 = POST
-    int sd[24], sk[24], sz[24], sp[24];
-    int top = 0;
-    sd[0] = d; sk[0] = 0; sz[0] = zero_init; sp[0] = 0;
-    while (top >= 0) {
-        int cd = sd[top];
-        int plo, phi;
-        diag_range(cd, h.pi, h.qi, plo, phi);
-        if (sp[top] == 0) {
-            for (int p = plo; p <= phi; ++p) visit_pre(h, p, cd + 2 - p, sz[top], cp.nu1);
-            if (cd == 0) { --top; continue; }
-            sp[top] = 1;
-            sk[top] = 0;
-        }
-        if (sp[top] == 1) {
-            if (sk[top] < cp.mu) {
-                int zi = (sk[top] == 0);
-                sk[top] += 1;
-                ++top;
-                sd[top] = cd - 1; sk[top] = 0; sz[top] = zi; sp[top] = 0;
-                continue;
-            }
-            sp[top] = 2;
-        }
-        for (int p = plo; p <= phi; ++p) visit_post(h, p, cd + 2 - p, cp.nu2, (T)cp.omega);
-        --top;
-    }
-}
-
 // ----------------------------------------------------------------- kernels --
 
 template <class T>
@@ -371,13 +344,271 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
     visit_post(h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
-template <class T>
-__global__ void k_low(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int d, int calls, int zero_init,
-                      CycleParams cp)
+// ------------------------------------------------- warp-resident recursion --
+//
+// Diagonals d <= kDW of an item's hierarchy are visited 2^(L-d) times per
+// cycle (Algorithm 1 with mu = 2) but hold only a few hundred unknowns, so
+// their cost is the latency of the dependent phases, not bandwidth.  One warp
+// owns one item: u, b and the two face-coefficient arrays of every grid with
+// p + q <= kDW + 2 live in shared memory (padded node layout, triangle order
+// p major), all grids of a diagonal advance together in one phase, and phases
+// are separated by __syncwarp only.
+
+constexpr int kDW = 4;
+constexpr int kLowWarps = 4;
+
+__host__ __device__ constexpr int low_nodes(int p, int q) { return ((1 << p) + 1) * ((1 << q) + 1); }
+__host__ __device__ constexpr int low_total()
 {
-    TaskRef t = resolve(cx);
-    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    for (int c = 0; c < calls; ++c) cta_mu_cycle(h, d, c == 0 ? zero_init : 0, cp);
+    int o = 0;
+    for (int p = 1; p <= kDW + 1; ++p)
+        for (int q = 1; q <= kDW + 2 - p; ++q) o += low_nodes(p, q);
+    return o;
+}
+constexpr int kLowNodes = low_total();
+
+template <class T>
+struct WGrid {
+    T* u;
+    T* b;
+    const T* ax;
+    const T* ay;
+    int nx, ny;
+};
+
+template <class T>
+struct WarpLow {
+    T* u;
+    T* b;
+    T* ax;
+    T* ay;
+    const int (*toff)[kDW + 2];
+    int pi, qi;  // item top (rectangle)
+    int lane;
+    __device__ WGrid<T> grid(int p, int q) const
+    {
+        const int o = toff[p][q];
+        return WGrid<T>{u + o, b + o, ax + o, ay + o, 1 << p, 1 << q};
+    }
+};
+
+template <class T>
+__device__ __forceinline__ T w_res_at(const WGrid<T>& g, int c, int W)
+{
+    T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
+    T Au = (aw + ae + as + an) * g.u[c] - (aw * g.u[c - 1] + ae * g.u[c + 1]) - (as * g.u[c - W] + an * g.u[c + W]);
+    return g.b[c] - Au;
+}
+
+// Red-black sweeps over all grids of diagonal d (grid (p,q) has 2^(p-1) slots
+// per row for each colour; slot kk of row j is node i = first + 2 kk).
+template <class T>
+__device__ __forceinline__ void w_sweeps(const WarpLow<T>& w, int d, int plo, int phi, int sweeps)
+{
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int p = plo; p <= phi; ++p) {
+                const int q = d + 2 - p;
+                WGrid<T> g = w.grid(p, q);
+                const int W = g.nx + 1, sh = p - 1, n = (g.ny - 1) << sh;
+                for (int k = w.lane; k < n; k += 32) {
+                    const int j = 1 + (k >> sh), kk = k & ((1 << sh) - 1);
+                    const int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
+                    if (i >= g.nx) continue;
+                    const int c = j * W + i;
+                    T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
+                    T nb = (aw * g.u[c - 1] + ae * g.u[c + 1]) + (as * g.u[c - W] + an * g.u[c + W]);
+                    g.u[c] = (g.b[c] + nb) * rcp_of(aw + ae + as + an);
+                }
+            }
+            __syncwarp();
+        }
+}
+
+template <class T, int D>
+__device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu1)
+{
+    if constexpr (D == 0) {
+        WGrid<T> g = w.grid(1, 1);
+        if (w.lane == 0) g.u[4] = g.b[4] * rcp_of(g.ax[3] + g.ax[4] + g.ay[1] + g.ay[4]);
+        __syncwarp();
+    } else {
+        int plo, phi;
+        diag_range(D, w.pi, w.qi, plo, phi);
+        if (zero_init) {
+            for (int p = plo; p <= phi; ++p) {
+                WGrid<T> g = w.grid(p, D + 2 - p);
+                const int n = (g.nx + 1) * (g.ny + 1);
+                for (int k = w.lane; k < n; k += 32) g.u[k] = T(0);
+            }
+            __syncwarp();
+        }
+        w_sweeps(w, D, plo, phi, nu1);
+        // restriction (Eq. (2.3)) in two passes: x-children are set, y-children are
+        // set or completed, so a two-parent child gets R_x/2 + R_y/2
+        for (int p = max(plo, 2); p <= phi; ++p) {
+            const int q = D + 2 - p;
+            WGrid<T> g = w.grid(p, q);
+            WGrid<T> c = w.grid(p - 1, q);
+            const T wgt = (q < w.qi) ? T(0.5) : T(1);
+            const int W = g.nx + 1, shc = p - 1, Wc = (1 << shc) + 1, n = (g.ny - 1) << shc;
+            for (int k = w.lane; k < n; k += 32) {
+                const int ic = k & ((1 << shc) - 1), j = 1 + (k >> shc);
+                if (ic == 0) continue;
+                const int cc = j * W + 2 * ic;
+                T v = T(0.25) * (w_res_at(g, cc - 1, W) + T(2) * w_res_at(g, cc, W) + w_res_at(g, cc + 1, W));
+                c.b[j * Wc + ic] = wgt * v;
+            }
+        }
+        __syncwarp();
+        for (int p = plo; p <= phi; ++p) {
+            const int q = D + 2 - p;
+            if (q < 2) continue;
+            WGrid<T> g = w.grid(p, q);
+            WGrid<T> c = w.grid(p, q - 1);
+            const bool both = p < w.pi;  // child (p, q-1) also has the x-parent (p+1, q-1)
+            const int W = g.nx + 1, n = ((g.ny >> 1) - 1) << p;
+            for (int k = w.lane; k < n; k += 32) {
+                const int i = k & (g.nx - 1), jc = 1 + (k >> p);
+                if (i == 0) continue;
+                const int cc = 2 * jc * W + i;
+                T v = T(0.25) * (w_res_at(g, cc - W, W) + T(2) * w_res_at(g, cc, W) + w_res_at(g, cc + W, W));
+                if (both) c.b[jc * W + i] += T(0.5) * v;
+                else c.b[jc * W + i] = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <class T, int D>
+__device__ __forceinline__ void w_post(const WarpLow<T>& w, int nu2, T omega)
+{
+    int plo, phi;
+    diag_range(D, w.pi, w.qi, plo, phi);
+    for (int p = plo; p <= phi; ++p) {
+        const int q = D + 2 - p;
+        WGrid<T> g = w.grid(p, q);
+        const T* ucx = (p > 1) ? w.grid(p - 1, q).u : nullptr;
+        const T* ucy = (q > 1) ? w.grid(p, q - 1).u : nullptr;
+        const int W = g.nx + 1, n = (g.ny - 1) << p;
+        for (int k = w.lane; k < n; k += 32) {
+            const int i = k & (g.nx - 1), j = 1 + (k >> p);
+            if (i == 0) continue;
+            const int c = j * W + i;
+            T vx = T(0), vy = T(0);
+            if (ucx) {
+                const int Wc = (g.nx >> 1) + 1, r = j * Wc + (i >> 1);
+                vx = (i & 1) ? T(0.5) * (ucx[r] + ucx[r + 1]) : ucx[r];
+            }
+            if (ucy) {
+                const int r = (j >> 1) * W + i;
+                vy = (j & 1) ? T(0.5) * (ucy[r] + ucy[r + W]) : ucy[r];
+            }
+            T corr;
+            if (ucx && ucy) {
+                T cxv = g.ax[c - 1] + g.ax[c], cyv = g.ay[c - W] + g.ay[c];
+                T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+                corr = (x2 * s) * vx + (y2 * s) * vy;
+            } else {
+                corr = ucx ? vx : vy;
+            }
+            g.u[c] += omega * corr;
+        }
+    }
+    __syncwarp();
+    w_sweeps(w, D, plo, phi, nu2);
+}
+
+// One mu-cycle of Algorithm 1 at diagonal D, unrolled at compile time.
+template <class T, int D>
+__device__ void w_cycle(const WarpLow<T>& w, int zero_init, const CycleParams& cp)
+{
+    w_pre<T, D>(w, zero_init, cp.nu1);
+    if constexpr (D > 0) {
+        for (int k = 0; k < cp.mu; ++k) w_cycle<T, D - 1>(w, k == 0, cp);
+        w_post<T, D>(w, cp.nu2, (T)cp.omega);
+    }
+}
+
+template <class T>
+__device__ void w_mu_cycle(const WarpLow<T>& w, int d, int zero_init, const CycleParams& cp)
+{
+    static_assert(kDW == 4, "dispatch below covers diagonals 0..4");
+    switch (d) {
+    case 0: w_cycle<T, 0>(w, zero_init, cp); break;
+    case 1: w_cycle<T, 1>(w, zero_init, cp); break;
+    case 2: w_cycle<T, 2>(w, zero_init, cp); break;
+    case 3: w_cycle<T, 3>(w, zero_init, cp); break;
+    default: w_cycle<T, 4>(w, zero_init, cp); break;
+    }
+}
+
+// `calls` mu-cycles at diagonal dl <= kDW of each item, one warp per item.
+// Reads the coefficients of the item's grids with d <= dl and the right-hand
+// side of its diagonal-dl grids (combined from the parents' restrictions, or
+// the item's own residual when dl is its top); writes back u of diagonal dl.
+template <class T>
+__global__ void __launch_bounds__(kLowWarps * 32) k_low_warp(DevCtx cx, int64_t nitems, T* su, const T* sbx,
+                                                            const T* sby, const T* ax, const T* ay, int dl,
+                                                            int calls, int zero_init, CycleParams cp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int toff[kDW + 2][kDW + 2];
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int p = 1; p <= kDW + 1; ++p)
+            for (int q = 1; q <= kDW + 2 - p; ++q) {
+                toff[p][q] = o;
+                o += low_nodes(p, q);
+            }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it = (int64_t)blockIdx.x * kLowWarps + warp;
+    if (it >= nitems) return;  // no block-wide barrier below this point
+    const TaskRef t = resolve_at(cx, it);
+    const SampleInfo& S = cx.samples[t.s];
+    WarpLow<T> w;
+    T* base = (T*)smem_raw + (size_t)warp * 4 * kLowNodes;
+    w.u = base;
+    w.b = base + kLowNodes;
+    w.ax = base + 2 * kLowNodes;
+    w.ay = base + 3 * kLowNodes;
+    w.toff = toff;
+    w.pi = t.seg->pi;
+    w.qi = t.seg->qi;
+    w.lane = lane;
+    for (int k = lane; k < kLowNodes; k += 32) w.u[k] = T(0);
+    for (int p = 1; p <= min(w.pi, dl + 1); ++p)
+        for (int q = 1; q <= min(w.qi, dl + 2 - p); ++q) {
+            const int n = low_nodes(p, q), o = toff[p][q];
+            const int64_t co = S.node_off + grid_offset(p, q, S.Q);
+            for (int k = lane; k < n; k += 32) {
+                w.ax[o + k] = ax[co + k];
+                w.ay[o + k] = ay[co + k];
+            }
+            if (p + q - 2 == dl) {
+                const int64_t so = t.scr + grid_offset(p, q, w.qi);
+                const bool hx = p < w.pi, hy = q < w.qi;
+                for (int k = lane; k < n; k += 32) {
+                    T v;
+                    if (hx && hy) v = T(0.5) * sbx[so + k] + T(0.5) * sby[so + k];
+                    else if (hy) v = sby[so + k];
+                    else v = sbx[so + k];  // x-parent only, or the item's own residual
+                    w.b[o + k] = v;
+                }
+            }
+        }
+    __syncwarp();
+    for (int c = 0; c < calls; ++c) w_mu_cycle(w, dl, c == 0 ? zero_init : 0, cp);
+    int plo, phi;
+    diag_range(dl, w.pi, w.qi, plo, phi);
+    for (int p = plo; p <= phi; ++p) {
+        const int q = dl + 2 - p, n = low_nodes(p, q), o = toff[p][q];
+        T* dst = su + t.scr + grid_offset(p, q, w.qi);
+        for (int k = lane; k < n; k += 32) dst[k] = w.u[o + k];
+    }
 }
 
 // Coefficients on every grid (Sec. 2, direct discretisation on each grid).
@@ -525,7 +756,7 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
         if (step == 0) act = 1;  // at least one cycle
         else if (!(rr == rr) || isinf(rr)) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NONFINITE); }
         else if (rr <= eps) act = 0;
-        else if (step >= max_cycles) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED); }
+        else if (step >= max_cycles || rr > 1.0) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED); }
         else act = 1;
         sflag[t.sidx] = act;
         if (!act) {
@@ -777,7 +1008,7 @@ WsLayout layout_of(const Plan& pl, int precision)
 }
 
 constexpr int kThreads = 256;
-constexpr int kLowCut = 6;  // diagonals <= kLowCut of a hierarchy run inside one launch per item
+constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-resident, one launch
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
 struct Pinned {
@@ -870,6 +1101,8 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
 
     const CycleParams cp{prm.mu, prm.nu1, prm.nu2, prm.omega};
     const double es = sizeof(T);
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * 4 * kLowNodes * kLowWarps)));
 
     for (int L = 0; L <= pl.Lmax; ++L) {
         const std::vector<ItemType>& its = pl.stage_items[L];
@@ -995,8 +1228,11 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
             // one mu-cycle (Algorithm 1) of every active item
             bool launch_err = false;
             auto launch_low = [&](int d, int calls, int zi) {
+                const size_t shm = sizeof(T) * 4 * kLowNodes * kLowWarps;
+                const unsigned nb = (unsigned)((nitems_active + kLowWarps - 1) / kLowWarps);
                 prof_begin(K_LOW, st);
-                k_low<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, su, sbx, sby, ax, ay, d, calls, zi, cp);
+                k_low_warp<T><<<nb, kLowWarps * 32, shm, st>>>(ic, nitems_active, su, sbx, sby, ax, ay, d, calls, zi,
+                                                               cp);
                 prof_end(K_LOW, st, low_bytes, 0.0);
                 launch_err |= cudaGetLastError() != cudaSuccess;
             };
