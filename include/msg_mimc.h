@@ -153,6 +153,22 @@ int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, con
 int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
                          const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream);
 
+/* Allocation-free variant of mimc_differences (no counterpart in the paper).  */
+/* Same arguments, results and errors.  For callers that may not allocate     */
+/* device memory once running (device memory fully reserved by their own     */
+/* pool, or a loop that cannot pay for an allocator call): the per-sample     */
+/* table and p_tau go to a fixed 16 MiB array in this library's own device    */
+/* memory, held by every GPU that loads the library until the process exits.  */
+/* A batch needing more (24 bytes per sample plus 8 ld1 ld2 bytes for p_tau,   */
+/* so at most about 690 000 samples) is rejected with MSG_ERR_INVALID.  The    */
+/* first call made with a device current looks up the array's address on that */
+/* device; make that call before any stream capture.  All calls share the     */
+/* array and return after their work has finished on `stream`; calls that     */
+/* overlap on the GPU race.  The array holds no state a call needs: each call  */
+/* writes the whole table it reads.                                           */
+int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
+                                 const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Instrumentation (no counterpart in the paper).                           */
 /*                                                                          */

@@ -1,6 +1,9 @@
 // mimc.cu -- multi-index differences (Sec. 3, Eq. (3.2)) and the per-sample
 // estimator term Y (Eq. (3.6)).  Index arithmetic is integer; the differences
 // are formed in the order D_1 then D_2 of the worked example of Sec. 3.
+#include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -87,5 +90,113 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
     MSG_CHECK_LAUNCH();
     MSG_CUDA_TRY(cudaFreeAsync(dbuf, st));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host tables above must outlive the copies
+    return MSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of mimc_differences.
+//
+// For callers that may not allocate device memory once they are running (a
+// program whose device memory is all reserved by its own pool, or a loop that
+// cannot afford an allocator call), the per-sample offset table and the p_tau
+// table go to a fixed array in the library's own device memory instead of a
+// temporary from cudaMallocAsync.  The array is a file-scope __device__
+// symbol: every GPU that loads the library holds it until the process exits.
+// In host code its name is only a host-side stand-in, so the device address
+// is looked up with cudaGetSymbolAddress once per device (on the first call
+// made with that device current) and cached.
+// ---------------------------------------------------------------------------
+namespace msg {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// host staging of the same size: filled and copied under the lock, so the
+// entry point needs no host or device allocation either
+alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_dev[kMaxDevices] = {};
+
+int noalloc_scratch(void** out)
+{
+    int dev = -1;
+    MSG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("mimc_differences_noalloc: device ordinal out of range");
+        return MSG_ERR_UNSUPPORTED;
+    }
+    if (!g_noalloc_dev[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("mimc_differences_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return MSG_ERR_CUDA;
+        }
+        g_noalloc_dev[dev] = p;
+    }
+    *out = g_noalloc_dev[dev];
+    return MSG_OK;
+}
+
+}  // namespace
+}  // namespace msg
+
+extern "C" int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
+                                            const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y,
+                                            void* stream)
+{
+    clear_error();
+    if (S < 0 || p0 < 1 || q0 < 1) {
+        set_error("mimc_differences_noalloc: need S >= 0, p0 >= 1, q0 >= 1");
+        return MSG_ERR_INVALID;
+    }
+    if (S == 0) return MSG_OK;
+    if (!L || !Q || !dQ) { set_error("mimc_differences_noalloc: NULL pointer"); return MSG_ERR_INVALID; }
+    const size_t tb = sizeof(MimcSample) * (size_t)S;
+    const size_t tb_al = (tb + 255) / 256 * 256;
+    const size_t pb = ptau ? sizeof(double) * (size_t)std::max(ld1, 0) * (size_t)std::max(ld2, 0) : 0;
+    if (tb_al + pb > kNoAllocBytes) {
+        set_error("mimc_differences_noalloc: batch needs " + std::to_string(tb_al + pb) +
+                  " bytes of scratch, more than the fixed " + std::to_string(kNoAllocBytes) +
+                  " (at most about " + std::to_string((kNoAllocBytes - pb) / sizeof(MimcSample)) +
+                  " samples per call)");
+        return MSG_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    MimcSample* h = (MimcSample*)g_noalloc_host;
+    int64_t qo = 0, dof = 0;
+    int maxL1 = 0, maxL2 = 0;
+    for (int64_t i = 0; i < S; ++i) {
+        int l1 = L[2 * i], l2 = L[2 * i + 1];
+        if (l1 < 0 || l2 < 0 || p0 + l1 > 12 || q0 + l2 > 12) {
+            set_error("mimc_differences_noalloc: multi-index out of range");
+            return MSG_ERR_INVALID;
+        }
+        h[i] = MimcSample{l1, l2, qo, dof};
+        qo += (int64_t)(p0 + l1) * (q0 + l2);
+        dof += (int64_t)(l1 + 1) * (l2 + 1);
+        maxL1 = l1 > maxL1 ? l1 : maxL1;
+        maxL2 = l2 > maxL2 ? l2 : maxL2;
+    }
+    if (ptau && (ld1 <= maxL1 || ld2 <= maxL2)) {
+        set_error("mimc_differences_noalloc: ptau table smaller than the largest multi-index");
+        return MSG_ERR_INVALID;
+    }
+    if (ptau) memcpy(g_noalloc_host + tb_al, ptau, pb);
+    void* dbase = nullptr;
+    int rc = noalloc_scratch(&dbase);
+    if (rc != MSG_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* d = (char*)dbase;
+    MSG_CUDA_TRY(cudaMemcpyAsync(d, g_noalloc_host, tb_al + pb, cudaMemcpyHostToDevice, st));
+    const double* dp = ptau ? (const double*)(d + tb_al) : nullptr;
+    int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
+    k_mimc<<<blocks, 256, 0, st>>>((const MimcSample*)d, S, p0, q0, Q, dp, ld2, dQ, Y);
+    prof_count();
+    MSG_CHECK_LAUNCH();
+    // the host staging and the device array are reused by the next call
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));
     return MSG_OK;
 }

@@ -25,5 +25,7 @@ enum KernelClass {
 // They count launches always and record CUDA events on `st` while profiling is on.
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double bytes, double flops);
+// count one launch without recording events
+void prof_count();
 
 }  // namespace msg

@@ -231,3 +231,22 @@ def solve(PQ, Z, prm: SolverParams | None = None, stream=None):
     ws = torch.empty(msg_workspace_bytes(pq, prm), dtype=torch.uint8, device=dev)
     msg_solve_batch(pq, prm, Z, Q, status, cycles, relres, ws, stream)
     return Q, status, cycles, relres
+
+
+def mimc_differences_noalloc(L, p0: int, q0: int, Q, dQ, ptau=None, Y=None, stream=None):
+    """Same as mimc_differences, with its scratch in the library's fixed device array."""
+    lib = load()
+    fn = lib.mimc_differences_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int32
+    Lh = _host_i32(L).reshape(-1, 2)
+    if ptau is not None:
+        pt = np.ascontiguousarray(np.asarray(ptau, dtype=np.float64))
+        ld1, ld2 = pt.shape
+        pp = pt.ctypes.data_as(ctypes.c_void_p)
+    else:
+        ld1 = ld2 = 0
+        pp = None
+    _check(fn(Lh.ctypes.data_as(ctypes.c_void_p), Lh.shape[0], p0, q0, _ptr(Q), pp, ld1, ld2, _ptr(dQ), _ptr(Y),
+              _stream(stream)))
