@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=0, help="oracle samples for the CPU baseline (0: one per core)")
     return ap.parse_args()
 
@@ -210,6 +211,15 @@ def ours(a, rank, world, local_rank):
     Y = torch.empty(S, dtype=torch.float64, device=dev)
     seed = 20190729
 
+    tuned = None
+    if not a.no_autotune:
+        from paper_1907_12334_gb300 import autotune
+
+        msg.msg_normals(seed, 0, S, M, xi)
+        msg.sample_field(prep, npts, M, gemm, xi, Z)
+        prm = autotune.tune(PQ, Z.reshape(-1), prm, sample=min(S, 512))
+        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps}
+
     def step(k):
         s0 = (k * world + rank) * S
         msg.msg_normals(seed, s0, S, M, xi)
@@ -316,7 +326,7 @@ def ours(a, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "S_per_gpu": S, "P": P, "Q": Q, "M": M, "eps": a.eps,
                        "omega": a.omega, "l2": "inputs larger than L2 (Z alone is 8.6 GB per step)",
-                       "converged_fraction": conv_frac},
+                       "converged_fraction": conv_frac, "launch_shapes": tuned},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -76,6 +76,8 @@ typedef struct {
     int32_t precision;  /* MSG_PREC_* */
     int32_t qoi;        /* MSG_QOI_* */
     int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
+    int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 256; multiple of 32) */
+    int32_t tune_low_warps; /* launch shape: items per CTA of the warp-resident kernel (0: 4; 1..8) */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */

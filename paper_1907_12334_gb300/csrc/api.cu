@@ -23,7 +23,6 @@ struct Prof {
     std::vector<cudaEvent_t> pool;
     size_t next = 0;
     std::vector<Rec> recs;
-    cudaEvent_t pending_start[K_NCLASS];
     cudaEvent_t take()
     {
         if (next == pool.size()) {
@@ -34,6 +33,7 @@ struct Prof {
         return pool[next++];
     }
 } g_prof;
+thread_local cudaEvent_t t_pending_start[K_NCLASS];  // begin events of this thread's open launches
 }  // namespace
 
 void set_error(const std::string& what) { g_last_error = what; }
@@ -45,7 +45,7 @@ void prof_begin(int cls, cudaStream_t st)
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.take();
     cudaEventRecord(e, st);
-    g_prof.pending_start[cls] = e;
+    t_pending_start[cls] = e;
 }
 
 void prof_end(int cls, cudaStream_t st, double bytes, double flops)
@@ -55,7 +55,7 @@ void prof_end(int cls, cudaStream_t st, double bytes, double flops)
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.take();
     cudaEventRecord(e, st);
-    g_prof.recs.push_back(Rec{g_prof.pending_start[cls], e, cls, bytes, flops});
+    g_prof.recs.push_back(Rec{t_pending_start[cls], e, cls, bytes, flops});
 }
 
 void prof_count() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -1,17 +1,322 @@
-// kl_tc.cu -- tcgen05 BF16x3 KL contraction (placeholder until the kernel lands).
+// kl_tc.cu -- KL contraction Z = Phi diag(sqrt(lambda)) xi on the 5th-generation
+// tensor cores (tcgen05), BF16x3 split products with FP32 accumulation.
+//
+// Z[s][x] = sum_m A[s][m] B[x][m] with A = sqrt(lambda) * xi (samples x terms)
+// and B = Phi (points x terms).  Each operand v is split into bf16 parts
+// v = hi + lo + O(2^-16 |v|); the product uses hi*hi + hi*lo + lo*hi (the
+// lo*lo term and the remainders are below the FP32 accumulation of a 400-term
+// sum of unit-scale products), so Z carries a relative error of about 1e-5 of
+// sum_m |A B| -- the sampler is not the FP64 path; its error is stated per
+// result in the tests.
+//
+// One CTA computes a 128 (samples) x 256 (points) tile of Z: accumulators in
+// 256 TMEM columns, K in chunks of 64 bf16 staged through two shared-memory
+// stages in the 128-byte-swizzled K-major layout the UMMA descriptors expect.
+// A is split on the fly from FP64 xi and sqrt(lambda); B (Phi) is split once
+// by kl_tc_prepare into zero-padded [Np][Kp] bf16 arrays.  One elected thread
+// issues the MMAs and commits them to an mbarrier per stage; every wait is
+// bounded and a timeout sets an error flag instead of hanging.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kl_tc.cuh"
+#include "prof.cuh"
 
 namespace msg {
-size_t kl_tc_prepared_bytes(int64_t, int32_t) { return 0; }
-int32_t kl_tc_prepare(const double*, const double*, int64_t, int32_t, void*, cudaStream_t)
+
+namespace {
+
+constexpr int kTM = 128;  // samples per tile (UMMA M)
+constexpr int kTN = 256;  // points per tile (UMMA N)
+constexpr int kTK = 64;   // K chunk: 64 bf16 = one 128-byte swizzle row
+constexpr int kThreadsTC = 256;
+constexpr int kAbytes = kTM * kTK * 2;       // 16 KB per A part
+constexpr int kBbytes = kTN * kTK * 2;       // 32 KB per B part
+constexpr int kStageBytes = 2 * kAbytes + 2 * kBbytes;  // hi+lo of A and B: 96 KB
+constexpr int kSmemBytes = 2 * kStageBytes + 1024;      // two stages + alignment slack
+constexpr long long kSpinLimit = 1ll << 22;             // bounded mbarrier waits (seconds)
+
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+__device__ int g_tc_error;  // set by a kernel whose mbarrier wait ran out
+
+// Byte offset of element (r, k), 0 <= k < 64, in a K-major tile with the
+// 128-byte swizzle: 8-row atoms of 1024 bytes, 16-byte chunk c of row rr
+// stored at chunk position c ^ rr.
+__device__ __forceinline__ uint32_t sw128(int r, int chunk) { return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4); }
+
+// tcgen05 shared-memory matrix descriptor: start address >> 4 in bits 0-13,
+// leading byte offset >> 4 in 16-29 (unused by swizzled K-major tiles),
+// stride byte offset >> 4 in 32-45 (1024: next 8-row atom), descriptor
+// version 1 in bits 46-47, swizzle mode 2 (128-byte) in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
-    set_error("BF16X3 mode not built");
-    return MSG_ERR_UNSUPPORTED;
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
-int32_t kl_tc_sample(const void*, int64_t, int32_t, const double*, int64_t, void*, int32_t, cudaStream_t)
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+__host__ __device__ constexpr uint32_t instr_desc()
 {
-    set_error("BF16X3 mode not built");
-    return MSG_ERR_UNSUPPORTED;
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Wait until the mbarrier phase with the given parity has completed; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Split of FP64 values into bf16 hi/lo.
+__device__ __forceinline__ void split2(double v, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    hi = __double2bfloat16(v);
+    lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+}
+
+__global__ void k_split_phi(const double* Phi, int64_t npts, int M, int64_t Kp, int64_t Np, __nv_bfloat16* Bhi,
+                            __nv_bfloat16* Blo)
+{
+    const int64_t n = Np * Kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = e / Kp, m = e % Kp;
+        double v = (x < npts && m < M) ? Phi[x * M + m] : 0.0;
+        __nv_bfloat16 h, l;
+        split2(v, h, l);
+        Bhi[e] = h;
+        Blo[e] = l;
+    }
+}
+
+template <class TZ>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_kl_tc(const __nv_bfloat16* __restrict__ Bhi, const __nv_bfloat16* __restrict__ Blo,
+            const double* __restrict__ sl, const double* __restrict__ xi, int64_t npts, int M, int64_t Kp, int64_t S,
+            TZ* __restrict__ Z)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 1024-aligned stage buffers (swizzle atoms must start on 1024 bytes)
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char* base = smem_raw + (((raw + 1023) & ~1023u) - raw);
+    const int64_t s0 = (int64_t)blockIdx.y * kTM, x0 = (int64_t)blockIdx.x * kTN;
+
+    if (warp == 0) {  // TMEM: 128 lanes x 256 FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                     "r"(kTN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_slot;
+
+    const int nchunks = (int)(Kp / kTK);
+    const uint32_t idesc = instr_desc();
+    bool ok = true;
+    for (int kc = 0; kc < nchunks; ++kc) {
+        const int st = kc & 1;
+        unsigned char* sA_hi = base + st * kStageBytes;
+        unsigned char* sA_lo = sA_hi + kAbytes;
+        unsigned char* sB_hi = sA_lo + kAbytes;
+        unsigned char* sB_lo = sB_hi + kBbytes;
+        if (kc >= 2) ok &= mbar_wait(&bars[st], ((kc >> 1) - 1) & 1);  // the MMAs that read this stage are done
+        // A chunk: 128 rows x 8 chunks of 8 terms, split on the fly
+        for (int t = tid; t < kTM * 8; t += kThreadsTC) {
+            const int r = t >> 3, c = t & 7;
+            const int64_t s = s0 + r;
+            __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int m = kc * kTK + c * 8 + j;
+                double v = (s < S && m < M) ? sl[m] * xi[s * M + m] : 0.0;
+                split2(v, h[j], l[j]);
+            }
+            const uint32_t off = sw128(r, c);
+            *reinterpret_cast<uint4*>(sA_hi + off) = *reinterpret_cast<const uint4*>(h);
+            *reinterpret_cast<uint4*>(sA_lo + off) = *reinterpret_cast<const uint4*>(l);
+        }
+        // B chunk: 256 rows x 8 chunks, already split and zero padded
+        for (int t = tid; t < kTN * 8; t += kThreadsTC) {
+            const int r = t >> 3, c = t & 7;
+            const int64_t g = (x0 + r) * Kp + (int64_t)kc * kTK + c * 8;
+            const uint32_t off = sw128(r, c);
+            *reinterpret_cast<uint4*>(sB_hi + off) = *reinterpret_cast<const uint4*>(Bhi + g);
+            *reinterpret_cast<uint4*>(sB_lo + off) = *reinterpret_cast<const uint4*>(Blo + g);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make the stores visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(sA_hi), a_lo = smem_u32(sA_lo);
+            const uint32_t b_hi = smem_u32(sB_hi), b_lo = smem_u32(sB_lo);
+#pragma unroll
+            for (int k16 = 0; k16 < kTK / 16; ++k16) {
+                const uint32_t ko = k16 * 32;  // 16 bf16 = 32 bytes along the swizzled row
+                const uint32_t first = (kc == 0 && k16 == 0) ? 0u : 1u;
+                mma_bf16(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), idesc, first);
+                mma_bf16(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1u);
+                mma_bf16(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
+            }
+            mma_commit(&bars[st]);
+        }
+    }
+    // wait for the last one or two stages' MMAs
+    if (nchunks >= 2) ok &= mbar_wait(&bars[(nchunks - 2) & 1], ((nchunks - 2) >> 1) & 1);
+    if (nchunks >= 1) ok &= mbar_wait(&bars[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (lane == 0) atomicExch(&g_tc_error, 1);
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 128 (w / 4) .. +127
+        const int lane_base = 32 * (warp & 3), col_base = 128 * (warp >> 2);
+        const int64_t s = s0 + lane_base + lane;
+        for (int cb = 0; cb < 128; cb += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(col_base + cb), v);
+            if (s < S) {
+                const int64_t xb = x0 + col_base + cb;
+                TZ* out = Z + s * npts + xb;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (xb + k < npts) out[k] = (TZ)v[k];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN) : "memory");
+}
+
+struct TcLayout {
+    int64_t Kp, Np;
+    size_t hi, lo, sl, total;
+};
+
+TcLayout tc_layout(int64_t npts, int32_t M)
+{
+    TcLayout L{};
+    L.Kp = round_up(M, kTK);
+    L.Np = round_up(npts, kTN);
+    const size_t part = (size_t)L.Np * L.Kp * sizeof(__nv_bfloat16);
+    L.hi = 0;
+    L.lo = (part + 255) / 256 * 256;
+    L.sl = L.lo + L.lo;
+    L.total = L.sl + ((sizeof(double) * M + 255) / 256 * 256);
+    return L;
+}
+
+}  // namespace
+
+size_t kl_tc_prepared_bytes(int64_t npts, int32_t M) { return tc_layout(npts, M).total; }
+
+int32_t kl_tc_prepare(const double* Phi, const double* sqrt_lambda, int64_t npts, int32_t M, void* prepared,
+                      cudaStream_t st)
+{
+    const TcLayout L = tc_layout(npts, M);
+    char* b = (char*)prepared;
+    prof_begin(K_KL, st);
+    k_split_phi<<<152 * 8, 256, 0, st>>>(Phi, npts, M, L.Kp, L.Np, (__nv_bfloat16*)(b + L.hi),
+                                          (__nv_bfloat16*)(b + L.lo));
+    prof_end(K_KL, st, 8.0 * npts * M + 4.0 * L.Np * L.Kp, 0.0);
+    MSG_CHECK_LAUNCH();
+    MSG_CUDA_TRY(cudaMemcpyAsync(b + L.sl, sqrt_lambda, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
+    return MSG_OK;
+}
+
+int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, const double* xi, int64_t S, void* Z,
+                     int32_t z_fp32, cudaStream_t st)
+{
+    const TcLayout L = tc_layout(npts, M);
+    if ((S + kTM - 1) / kTM > 65535) { set_error("sample_field: too many samples for one call"); return MSG_ERR_INVALID; }
+    const char* b = (const char*)prepared;
+    const __nv_bfloat16* Bhi = (const __nv_bfloat16*)(b + L.hi);
+    const __nv_bfloat16* Blo = (const __nv_bfloat16*)(b + L.lo);
+    const double* sl = (const double*)(b + L.sl);
+    dim3 grid((unsigned)(L.Np / kTN), (unsigned)((S + kTM - 1) / kTM));
+    int zero = 0;
+    MSG_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    prof_begin(K_KL, st);
+    if (z_fp32) {
+        MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        k_kl_tc<float><<<grid, kThreadsTC, kSmemBytes, st>>>(Bhi, Blo, sl, xi, npts, M, L.Kp, S, (float*)Z);
+    } else {
+        MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        k_kl_tc<double><<<grid, kThreadsTC, kSmemBytes, st>>>(Bhi, Blo, sl, xi, npts, M, L.Kp, S, (double*)Z);
+    }
+    // algorithmic work: 3 split products of 2 npts M S flops; bytes: Phi parts, xi, Z
+    prof_end(K_KL, st, 4.0 * npts * M + 8.0 * S * M + (z_fp32 ? 4.0 : 8.0) * S * npts, 6.0 * npts * M * S);
+    MSG_CHECK_LAUNCH();
+    int err = 0;
+    MSG_CUDA_TRY(cudaMemcpyFromSymbolAsync(&err, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("sample_field: tensor-core pipeline wait timed out");
+        return MSG_ERR_CUDA;
+    }
+    return MSG_OK;
+}
+
 }  // namespace msg

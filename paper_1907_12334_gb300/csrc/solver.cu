@@ -25,9 +25,16 @@
 //   su, sbx, sby scratch of the active items' hierarchies: correction e and the
 //                restrictions received from the x-parent and the y-parent.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -355,7 +362,7 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
 // are separated by __syncwarp only.
 
 constexpr int kDW = 4;
-constexpr int kLowWarps = 4;
+constexpr int kLowWarpsMax = 8;  // warps (items) per CTA of the warp-resident kernel: 1..8, default 4
 
 __host__ __device__ constexpr int low_nodes(int p, int q) { return ((1 << p) + 1) * ((1 << q) + 1); }
 __host__ __device__ constexpr int low_total()
@@ -549,7 +556,7 @@ __device__ void w_mu_cycle(const WarpLow<T>& w, int d, int zero_init, const Cycl
 // side of its diagonal-dl grids (combined from the parents' restrictions, or
 // the item's own residual when dl is its top); writes back u of diagonal dl.
 template <class T>
-__global__ void __launch_bounds__(kLowWarps * 32) k_low_warp(DevCtx cx, int64_t nitems, T* su, const T* sbx,
+__global__ void __launch_bounds__(kLowWarpsMax * 32) k_low_warp(DevCtx cx, int64_t nitems, T* su, const T* sbx,
                                                             const T* sby, const T* ax, const T* ay, int dl,
                                                             int calls, int zero_init, CycleParams cp)
 {
@@ -565,7 +572,7 @@ __global__ void __launch_bounds__(kLowWarps * 32) k_low_warp(DevCtx cx, int64_t 
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = (int64_t)blockIdx.x * kLowWarps + warp;
+    const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (it >= nitems) return;  // no block-wide barrier below this point
     const TaskRef t = resolve_at(cx, it);
     const SampleInfo& S = cx.samples[t.s];
@@ -726,9 +733,9 @@ __device__ double block_sum(double v)
 // FP64 residual of the item's grid, convergence decision, and the right-hand
 // side of the next correction cycle (written into the item's scratch).
 template <class T>
-__global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, const double* ay64, T* sbx, int step,
-                           int max_cycles, double eps, int* sflag, int* cycles, double* relres, int* status,
-                           int* counter)
+__global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, const double* ay64, T* sbx,
+                           int max_cycles, double eps, int* nstep, int* sflag, int* cycles, double* relres,
+                           int* status, int* counter)
 {
     TaskRef t = resolve(cx);
     const SampleInfo& S = cx.samples[t.s];
@@ -751,6 +758,7 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
     }
     double ss = block_sum(acc);
     if (threadIdx.x == 0) {
+        const int step = nstep[t.item];  // cycles done on this item so far
         double rr = sqrt(ss / (double)n);  // ||b|| with b = 1 on n interior nodes
         int act;
         if (step == 0) act = 1;  // at least one cycle
@@ -763,6 +771,7 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
             cycles[t.item] = step;
             relres[t.item] = rr;
         } else {
+            nstep[t.item] = step + 1;
             atomicAdd(counter, 1);
         }
     }
@@ -848,6 +857,7 @@ struct Plan {
     std::vector<SampleInfo> samples;
     std::vector<int> perm;  // samples ordered by group
     std::vector<int> gpos;  // position of each sample inside its group
+    std::vector<int> sgroup; // group of each sample
     std::vector<Group> groups;
     int Lmax = -1;
     std::vector<std::vector<Group>> stage_groups;   // [L]: groups with the stage's scratch layout
@@ -874,6 +884,14 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         return MSG_ERR_INVALID;
     }
     if (prm->qoi < 0 || prm->qoi > 3) { set_error("qoi out of range"); return MSG_ERR_INVALID; }
+    if (prm->tune_block != 0 && (prm->tune_block < 32 || prm->tune_block > 1024 || prm->tune_block % 32)) {
+        set_error("tune_block must be 0 or a multiple of 32 in [32, 1024]");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->tune_low_warps < 0 || prm->tune_low_warps > kLowWarpsMax) {
+        set_error("tune_low_warps must be in [0, 8]");
+        return MSG_ERR_INVALID;
+    }
     if (prm->coef != MSG_COEF_SERIES && prm->coef != MSG_COEF_INJECT) {
         set_error("coef must be MSG_COEF_SERIES or MSG_COEF_INJECT");
         return MSG_ERR_INVALID;
@@ -929,6 +947,7 @@ void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
     }
     pl.perm.resize(S);
     pl.gpos.resize(S);
+    pl.sgroup = sample_group;
     for (int64_t i = 0; i < S; ++i) {
         int g = sample_group[i];
         pl.gpos[i] = cnt[g] - pl.groups[g].start;
@@ -970,9 +989,11 @@ void build_plan(const int32_t* PQ, int64_t S, Plan& pl)
 }
 
 struct WsLayout {
-    size_t samples, perm, gpos, groups, allsegs, stepsegs, slist, sflag;
-    size_t cycles_i, relres_i, counter;
-    size_t u64, ax64, ay64, ax32, ay32, su, sbx, sby;
+    size_t samples, perm, gpos, groups, allsegs;
+    size_t nstep, cycles_i, relres_i;
+    size_t u64, ax64, ay64, ax32, ay32;
+    // per stage L: segment list, sample list, flags, counter, scratch (su, sbx, sby)
+    std::vector<size_t> segs, slist, sflag, counter, su, sbx, sby;
     size_t total;
 };
 
@@ -986,23 +1007,29 @@ WsLayout layout_of(const Plan& pl, int precision)
     w.gpos = take(sizeof(int) * pl.S);
     w.groups = take(sizeof(Group) * pl.groups.size() * (pl.Lmax + 2));
     w.allsegs = take(sizeof(Segment) * pl.all_segs.size());
-    w.stepsegs = take(sizeof(Segment) * pl.max_segs);
-    w.slist = take(sizeof(int) * pl.max_stage_items);
-    w.sflag = take(sizeof(int) * pl.max_stage_items);
+    w.nstep = take(sizeof(int) * pl.total_q);
     w.cycles_i = take(sizeof(int) * pl.total_q);
     w.relres_i = take(sizeof(double) * pl.total_q);
-    w.counter = take(sizeof(int) * 4);
     w.u64 = take(sizeof(double) * pl.total_nodes);
     w.ax64 = take(sizeof(double) * pl.total_nodes);
     w.ay64 = take(sizeof(double) * pl.total_nodes);
-    size_t es = precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    const size_t es = precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
     if (precision == MSG_PREC_MIXED) {
         w.ax32 = take(sizeof(float) * pl.total_nodes);
         w.ay32 = take(sizeof(float) * pl.total_nodes);
     }
-    w.su = take(es * pl.scratch_nodes);
-    w.sbx = take(es * pl.scratch_nodes);
-    w.sby = take(es * pl.scratch_nodes);
+    for (int L = 0; L <= pl.Lmax; ++L) {
+        int64_t nseg = 0, scr = 0;
+        for (const ItemType& it : pl.stage_items[L]) nseg += 1 + (int64_t)it.pi * it.qi;
+        for (const Group& g : pl.stage_groups[L]) scr += g.scr_per_sample * g.count;
+        w.segs.push_back(take(sizeof(Segment) * nseg));
+        w.slist.push_back(take(sizeof(int) * pl.stage_nitems[L]));
+        w.sflag.push_back(take(sizeof(int) * pl.stage_nitems[L]));
+        w.counter.push_back(take(sizeof(int) * 4));
+        w.su.push_back(take(es * scr));
+        w.sbx.push_back(take(es * scr));
+        w.sby.push_back(take(es * scr));
+    }
     w.total = off + 256;
     return w;
 }
@@ -1013,27 +1040,341 @@ constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-re
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
 struct Pinned {
     void* p = nullptr;
-    size_t bytes = 0;
     ~Pinned() { if (p) cudaFreeHost(p); }
     int alloc(size_t b)
     {
         if (cudaMallocHost(&p, std::max<size_t>(b, 64)) != cudaSuccess) { p = nullptr; return MSG_ERR_CUDA; }
-        bytes = b;
         return MSG_OK;
     }
+};
+
+// Hand-over of samples between the stage workers.
+struct StageQueues {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::vector<int>> ready;  // [L]: samples whose stage L may start
+    std::vector<char> done;               // [L]: stage L worker finished
+    bool abort = false;
 };
 
 }  // namespace
 
 // ------------------------------------------------------------- entry point --
 
+// Everything one stage worker needs (shared, read-only during the solve).
+template <class T>
+struct SolveCtx {
+    const Plan& pl;
+    const WsLayout& wl;
+    char* ws;
+    const msg_params& prm;
+    const double* Z;
+    int32_t* stat;
+    DevCtx base;
+    const Group* dgroups;
+    double* u64;
+    const double* ax64;
+    const double* ay64;
+    const T* ax;
+    const T* ay;
+    int* nstep;
+    int* cyc;
+    double* rel;
+    CycleParams cp;
+    int block;      // threads per CTA of the PRE/POST visit kernels
+    int low_warps;  // items (warps) per CTA of the warp-resident kernel
+};
+
+// Stage L of FMSG for the samples handed over by stage L-1: cubic
+// interpolation when a sample enters, then defect-correction cycles of every
+// item until it meets eps (or stops), each step on this stage's own stream.
+// A sample moves on to stage L+1 as soon as all its stage-L items are done.
+template <class T>
+static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream_t st)
+{
+    const Plan& pl = C.pl;
+    const WsLayout& wl = C.wl;
+    const std::vector<ItemType>& its = pl.stage_items[L];
+    const std::vector<Group>& hsg = pl.stage_groups[L];
+    const size_t ng = pl.groups.size();
+    const Group* sg = C.dgroups + ng * (1 + L);
+    T* su = (T*)(C.ws + wl.su[L]);
+    T* sbx = (T*)(C.ws + wl.sbx[L]);
+    T* sby = (T*)(C.ws + wl.sby[L]);
+    int* sflag = (int*)(C.ws + wl.sflag[L]);
+    int* slist = (int*)(C.ws + wl.slist[L]);
+    int* counter = (int*)(C.ws + wl.counter[L]);
+    Segment* dsegs = (Segment*)(C.ws + wl.segs[L]);
+    const double es = sizeof(T);
+
+    // item types of each group at this stage, and per-sample countdown of open items
+    std::vector<std::vector<int>> types_of(ng);
+    for (size_t k = 0; k < its.size(); ++k) types_of[its[k].g].push_back((int)k);
+    std::vector<int> open(pl.S, 0);
+
+    int64_t nseg_max = 0;
+    for (const ItemType& it : its) nseg_max += 1 + (int64_t)it.pi * it.qi;
+    Pinned pin;
+    const size_t flag_bytes = sizeof(int) * std::max<int64_t>(pl.stage_nitems[L], 1);
+    if (pin.alloc(64 + 2 * flag_bytes + sizeof(Segment) * std::max<int64_t>(nseg_max, 1)) != MSG_OK) {
+        set_error("cudaMallocHost failed");
+        return MSG_ERR_CUDA;
+    }
+    int* h_counter = (int*)pin.p;
+    int* h_flags = (int*)((char*)pin.p + 64);
+    int* h_list = (int*)((char*)pin.p + 64 + flag_bytes);
+    Segment* h_segs = (Segment*)((char*)pin.p + 64 + 2 * flag_bytes);
+
+    std::vector<std::vector<int>> active(its.size()), fresh(its.size());
+    size_t item_nseg = 0;
+    std::vector<size_t> dseg0(L + 1, 0), dnseg(L + 1, 0);
+    std::vector<double> dpre(L + 1, 0), dpost(L + 1, 0);
+    int64_t nitems = 0;
+    double item_pts = 0, low_bytes = 0;
+    // Upload per-item sample lists and segments for `lists` (item level first,
+    // then one list per diagonal above the warp cut when with_diag).
+    auto build_lists = [&](const std::vector<std::vector<int>>& lists, bool with_diag) -> int {
+        std::vector<int64_t> loff(its.size());
+        int64_t nl = 0;
+        item_pts = 0;
+        for (size_t k = 0; k < its.size(); ++k) {
+            loff[k] = nl;
+            for (int s : lists[k]) h_list[nl++] = s;
+            item_pts += (double)lists[k].size() * pts(its[k].pi, its[k].qi);
+        }
+        nitems = nl;
+        size_t ns = 0;
+        int64_t b = 0;
+        for (size_t k = 0; k < its.size(); ++k) {
+            if (lists[k].empty()) continue;
+            const ItemType& it = its[k];
+            h_segs[ns++] = Segment{it.g, it.pi, it.qi, it.pi, it.qi, b, (int64_t)lists[k].size(), loff[k], it.scr_slot,
+                                   it.stage_base};
+            b += (int64_t)lists[k].size();
+        }
+        item_nseg = ns;
+        if (with_diag) {
+            const int dl = std::min(L, kLowCut);
+            low_bytes = 0;
+            for (size_t k = 0; k < its.size(); ++k)
+                for (int pp = 1; pp <= its[k].pi; ++pp)
+                    for (int qq = 1; qq <= its[k].qi; ++qq) {
+                        const int dd = pp + qq - 2;
+                        if (dd > dl) continue;
+                        const double n = (double)lists[k].size() * pts(pp, qq);
+                        low_bytes += n * 2;
+                        if (dd == dl) low_bytes += n * ((pp < its[k].pi && qq < its[k].qi) ? 3 : 2);
+                    }
+            low_bytes *= es;
+            for (int d = kLowCut + 1; d <= L; ++d) {
+                dseg0[d] = ns;
+                b = 0;
+                dpre[d] = dpost[d] = 0;
+                for (size_t k = 0; k < its.size(); ++k) {
+                    if (lists[k].empty()) continue;
+                    const ItemType& it = its[k];
+                    for (int pp = std::max(1, d + 2 - it.qi); pp <= std::min(it.pi, d + 1); ++pp) {
+                        const int qq = d + 2 - pp;
+                        h_segs[ns++] = Segment{it.g, it.pi, it.qi, pp, qq, b, (int64_t)lists[k].size(), loff[k],
+                                               it.scr_slot, it.stage_base};
+                        b += (int64_t)lists[k].size();
+                        const double n = (double)lists[k].size() * pts(pp, qq);
+                        const double bw = (pp < it.pi && qq < it.qi) ? 2.0 : 1.0;
+                        const double ch = (pp > 1 ? 0.5 : 0.0) + (qq > 1 ? 0.5 : 0.0);
+                        dpre[d] += n * (bw + 2 + 1 + ch);
+                        dpost[d] += n * (ch + bw + 2 + 2);
+                    }
+                }
+                dnseg[d] = ns - dseg0[d];
+            }
+        }
+        MSG_CUDA_TRY(cudaMemcpyAsync(slist, h_list, sizeof(int) * std::max<int64_t>(nl, 1), cudaMemcpyHostToDevice, st));
+        MSG_CUDA_TRY(cudaMemcpyAsync(dsegs, h_segs, sizeof(Segment) * std::max<size_t>(ns, 1), cudaMemcpyHostToDevice,
+                                     st));
+        return MSG_OK;
+    };
+    auto ctx_of = [&](size_t seg0, size_t n) {
+        DevCtx c = C.base;
+        c.slist = slist;
+        c.groups = sg;
+        c.segs = dsegs + seg0;
+        c.nseg = (int)n;
+        return c;
+    };
+    auto finish = [&](int rc) {
+        std::lock_guard<std::mutex> lk(Qs.mu);
+        Qs.done[L] = 1;
+        if (rc != MSG_OK) Qs.abort = true;
+        Qs.cv.notify_all();
+        return rc;
+    };
+    int64_t open_items = 0;
+    // optional per-stage statistics on stderr (MSG_STAGE_STATS=1)
+    static const bool stats = getenv("MSG_STAGE_STATS") != nullptr;
+    int64_t n_steps = 0, n_item_cycles = 0, n_admitted = 0;
+    const auto t_start = std::chrono::steady_clock::now();
+    double t_first = -1.0;
+    struct StatsOut {
+        bool on; int L; int64_t *st, *ic, *ad; double* tf; std::chrono::steady_clock::time_point t0;
+        ~StatsOut()
+        {
+            if (!on) return;
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            fprintf(stderr, "[stage %2d] admitted %lld steps %lld item-cycles %lld first-admit %.1f ms done %.1f ms\n", L,
+                    (long long)*ad, (long long)*st, (long long)*ic, *tf, ms);
+        }
+    } stats_out{stats, L, &n_steps, &n_item_cycles, &n_admitted, &t_first, t_start};
+    for (;;) {
+        // ---- admit the samples stage L-1 has finished
+        std::vector<int> admitted;
+        {
+            std::unique_lock<std::mutex> lk(Qs.mu);
+            if (open_items == 0)
+                Qs.cv.wait(lk, [&] { return Qs.abort || !Qs.ready[L].empty() || (L == 0 || Qs.done[L - 1]); });
+            if (Qs.abort) return finish(MSG_OK);
+            admitted.swap(Qs.ready[L]);
+            if (admitted.empty() && open_items == 0 && (L == 0 || Qs.done[L - 1])) break;
+        }
+        // the previous step's uploads read the pinned staging that is rewritten below
+        if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("stage stream failed"); return finish(MSG_ERR_CUDA); }
+        if (!admitted.empty()) {
+            n_admitted += (int64_t)admitted.size();
+            if (t_first < 0)
+                t_first = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            for (auto& f : fresh) f.clear();
+            std::vector<int> pass_on;
+            for (int s : admitted) {
+                const int g = pl.sgroup[s];
+                if (types_of[g].empty()) { pass_on.push_back(s); continue; }  // no grid of this sample at stage L
+                open[s] = (int)types_of[g].size();
+                open_items += open[s];
+                for (int k : types_of[g]) fresh[k].push_back(s);
+            }
+            if (!pass_on.empty() && L < pl.Lmax) {
+                std::lock_guard<std::mutex> lk(Qs.mu);
+                for (int s : pass_on) Qs.ready[L + 1].push_back(s);
+                Qs.cv.notify_all();
+            }
+            int rc = build_lists(fresh, false);
+            if (rc != MSG_OK) return finish(rc);
+            if (nitems > 0) {
+                prof_begin(K_INTERP, st);
+                k_interp<<<(unsigned)nitems, kThreads, 0, st>>>(ctx_of(0, item_nseg), C.u64, C.ax64, C.ay64);
+                prof_end(K_INTERP, st, item_pts * (8.0 + 16.0 + 8.0), 0.0);
+                if (cudaGetLastError() != cudaSuccess) { set_error("k_interp launch"); return finish(MSG_ERR_CUDA); }
+            }
+            for (size_t k = 0; k < its.size(); ++k) active[k].insert(active[k].end(), fresh[k].begin(), fresh[k].end());
+            if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("stage stream failed"); return finish(MSG_ERR_CUDA); }
+        }
+        if (open_items == 0) continue;
+        // ---- residual, convergence decision
+        int rc = build_lists(active, false);
+        if (rc != MSG_OK) return finish(rc);
+        if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return finish(MSG_ERR_CUDA);
+        prof_begin(K_RESIDUAL, st);
+        k_residual<T><<<(unsigned)nitems, kThreads, 0, st>>>(ctx_of(0, item_nseg), C.u64, C.ax64, C.ay64, sbx,
+                                                             C.prm.max_cycles, C.prm.eps, C.nstep, sflag, C.cyc,
+                                                             C.rel, C.stat, counter);
+        prof_end(K_RESIDUAL, st, item_pts * (24.0 + es), 0.0);
+        if (cudaGetLastError() != cudaSuccess) { set_error("k_residual launch"); return finish(MSG_ERR_CUDA); }
+        if (cudaMemcpyAsync(h_counter, counter, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(h_flags, sflag, sizeof(int) * pl.stage_nitems[L], cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("stage step synchronisation failed");
+            return finish(MSG_ERR_CUDA);
+        }
+        // ---- retire finished items; samples whose stage-L items are all done move on
+        std::vector<int> completed;
+        for (size_t k = 0; k < its.size(); ++k) {
+            std::vector<int>& a = active[k];
+            size_t w = 0;
+            for (size_t r = 0; r < a.size(); ++r) {
+                const int s = a[r];
+                if (h_flags[its[k].stage_base + pl.gpos[s]]) { a[w++] = s; continue; }
+                --open_items;
+                if (--open[s] == 0) completed.push_back(s);
+            }
+            a.resize(w);
+        }
+        if (!completed.empty() && L < pl.Lmax) {
+            std::lock_guard<std::mutex> lk(Qs.mu);
+            for (int s : completed) Qs.ready[L + 1].push_back(s);
+            Qs.cv.notify_all();
+        }
+        if (*h_counter == 0) continue;
+        ++n_steps;
+        n_item_cycles += *h_counter;
+        // ---- one mu-cycle (Algorithm 1) of every active item
+        rc = build_lists(active, true);
+        if (rc != MSG_OK) return finish(rc);
+        DevCtx ic = ctx_of(0, item_nseg);
+        bool launch_err = false;
+        auto launch_low = [&](int d, int calls, int zi) {
+            const int lw = C.low_warps;
+            const size_t shm = sizeof(T) * 4 * kLowNodes * lw;
+            const unsigned nb = (unsigned)((nitems + lw - 1) / lw);
+            prof_begin(K_LOW, st);
+            k_low_warp<T><<<nb, lw * 32, shm, st>>>(ic, nitems, su, sbx, sby, C.ax, C.ay, d, calls, zi, C.cp);
+            prof_end(K_LOW, st, low_bytes, 0.0);
+            launch_err |= cudaGetLastError() != cudaSuccess;
+        };
+        auto launch_half = [&](int d, int pre, int zi) {
+            if (dnseg[d] == 0) return;
+            const Segment& last = h_segs[dseg0[d] + dnseg[d] - 1];
+            const int64_t nb = last.blk_start + last.count;
+            DevCtx c = ctx_of(dseg0[d], dnseg[d]);
+            prof_begin(pre ? K_PRE : K_POST, st);
+            if (pre) k_pre<T><<<(unsigned)nb, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+            else k_post<T><<<(unsigned)nb, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+            prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0);
+            launch_err |= cudaGetLastError() != cudaSuccess;
+        };
+        if (L <= kLowCut) {
+            launch_low(L, 1, 1);
+        } else {
+            struct Frame { int d, k, zi, phase; };
+            std::vector<Frame> stack;
+            stack.push_back({L, 0, 1, 0});
+            while (!stack.empty()) {
+                Frame& f = stack.back();
+                if (f.phase == 0) {
+                    launch_half(f.d, 1, f.zi);
+                    f.phase = 1;
+                    if (f.d - 1 <= kLowCut) {
+                        launch_low(f.d - 1, C.prm.mu, 1);
+                        f.phase = 2;
+                    }
+                    continue;
+                }
+                if (f.phase == 1) {
+                    if (f.k < C.prm.mu) {
+                        const int zi = (f.k == 0);
+                        f.k += 1;
+                        stack.push_back({f.d - 1, 0, zi, 0});
+                        continue;
+                    }
+                    f.phase = 2;
+                }
+                launch_half(f.d, 0, 0);
+                stack.pop_back();
+            }
+        }
+        if (launch_err) { set_error("kernel launch failed in the cycle schedule"); return finish(MSG_ERR_CUDA); }
+        prof_begin(K_UPDATE, st);
+        k_update<T><<<(unsigned)nitems, kThreads, 0, st>>>(ic, C.u64, su);
+        prof_end(K_UPDATE, st, item_pts * (16.0 + es), 0.0);
+        if (cudaGetLastError() != cudaSuccess) { set_error("k_update launch"); return finish(MSG_ERR_CUDA); }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return finish(MSG_ERR_CUDA);
+    return finish(MSG_OK);
+}
+
 template <class T>
 static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_params& prm, const double* Z,
                      double* Qout, int32_t* stat, int32_t* cycles_out, double* relres_out, cudaStream_t st)
 {
     const bool mixed = prm.precision == MSG_PREC_MIXED;
-    const size_t ng = pl.groups.size();
-    // ---- static tables
     std::vector<Group> gtab;  // [0]: groups, [1+L]: stage L groups
     gtab.insert(gtab.end(), pl.groups.begin(), pl.groups.end());
     for (int L = 0; L <= pl.Lmax; ++L) gtab.insert(gtab.end(), pl.stage_groups[L].begin(), pl.stage_groups[L].end());
@@ -1043,262 +1384,81 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.groups, gtab.data(), sizeof(Group) * gtab.size(), cudaMemcpyHostToDevice, st));
     MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.allsegs, pl.all_segs.data(), sizeof(Segment) * pl.all_segs.size(),
                                  cudaMemcpyHostToDevice, st));
-
-    double* u64 = (double*)(ws + wl.u64);
-    double* ax64 = (double*)(ws + wl.ax64);
-    double* ay64 = (double*)(ws + wl.ay64);
+    SolveCtx<T> C{pl, wl, ws, prm, Z, stat, DevCtx{}, (const Group*)(ws + wl.groups), (double*)(ws + wl.u64),
+                  (const double*)(ws + wl.ax64), (const double*)(ws + wl.ay64), nullptr, nullptr,
+                  (int*)(ws + wl.nstep), (int*)(ws + wl.cycles_i), (double*)(ws + wl.relres_i),
+                  CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kThreads,
+                  prm.tune_low_warps ? prm.tune_low_warps : 4};
     float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
     float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
-    T* su = (T*)(ws + wl.su);
-    T* sbx = (T*)(ws + wl.sbx);
-    T* sby = (T*)(ws + wl.sby);
-    const T* ax = mixed ? (const T*)ax32 : (const T*)ax64;
-    const T* ay = mixed ? (const T*)ay32 : (const T*)ay64;
-    int* cyc = (int*)(ws + wl.cycles_i);
-    double* rel = (double*)(ws + wl.relres_i);
-    int* counter = (int*)(ws + wl.counter);
-    int* sflag = (int*)(ws + wl.sflag);
-    int* slist = (int*)(ws + wl.slist);
-    Segment* stepsegs = (Segment*)(ws + wl.stepsegs);
-    const Group* dgroups = (const Group*)(ws + wl.groups);
+    C.ax = mixed ? (const T*)ax32 : (const T*)(ws + wl.ax64);
+    C.ay = mixed ? (const T*)ay32 : (const T*)(ws + wl.ay64);
+    C.base.samples = (const SampleInfo*)(ws + wl.samples);
+    C.base.gpos = (const int*)(ws + wl.gpos);
 
     MSG_CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(int32_t) * pl.S, st));
-    MSG_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * pl.total_nodes, st));
-
-    DevCtx base{};
-    base.samples = (const SampleInfo*)(ws + wl.samples);
-    base.gpos = (const int*)(ws + wl.gpos);
-
-    // ---- coefficients on every grid
+    MSG_CUDA_TRY(cudaMemsetAsync(C.u64, 0, sizeof(double) * pl.total_nodes, st));
+    MSG_CUDA_TRY(cudaMemsetAsync(C.nstep, 0, sizeof(int) * pl.total_q, st));
     {
-        DevCtx c = base;
+        DevCtx c = C.base;
         c.slist = (const int*)(ws + wl.perm);
-        c.groups = dgroups;
+        c.groups = C.dgroups;
         c.segs = (const Segment*)(ws + wl.allsegs);
         c.nseg = (int)pl.all_segs.size();
-        int64_t nb = pl.all_segs.empty() ? 0 : pl.all_segs.back().blk_start + pl.all_segs.back().count;
+        const int64_t nb = pl.all_segs.empty() ? 0 : pl.all_segs.back().blk_start + pl.all_segs.back().count;
         double nodes = 0;
         for (const Segment& s : pl.all_segs) nodes += (double)s.count * ((1 << s.p) + 1) * ((1 << s.q) + 1);
         prof_begin(K_COEFFS, st);
-        k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(c, Z, prm.coef, ax64, ay64, ax32, ay32);
+        k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(c, Z, prm.coef, (double*)(ws + wl.ax64), (double*)(ws + wl.ay64),
+                                                   ax32, ay32);
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-
-    // ---- host staging for the per-step lists: [counter | flags | sample list | segments]
-    const size_t flag_bytes = sizeof(int) * std::max<int64_t>(pl.max_stage_items, 1);
-    const size_t list_bytes = flag_bytes;
-    const size_t seg_bytes = sizeof(Segment) * std::max<int64_t>(pl.max_segs, 1);
-    Pinned pin;
-    if (pin.alloc(64 + flag_bytes + list_bytes + seg_bytes) != MSG_OK) {
-        set_error("cudaMallocHost failed");
-        return MSG_ERR_CUDA;
-    }
-    int* h_counter = (int*)pin.p;
-    int* h_flags = (int*)((char*)pin.p + 64);
-    int* h_list = (int*)((char*)pin.p + 64 + flag_bytes);
-    Segment* h_segs = (Segment*)((char*)pin.p + 64 + flag_bytes + list_bytes);
-
-    const CycleParams cp{prm.mu, prm.nu1, prm.nu2, prm.omega};
-    const double es = sizeof(T);
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes * kLowWarps)));
+                                      (int)(sizeof(T) * 4 * kLowNodes * kLowWarpsMax)));
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));
 
-    for (int L = 0; L <= pl.Lmax; ++L) {
-        const std::vector<ItemType>& its = pl.stage_items[L];
-        if (its.empty()) continue;
-        const std::vector<Group>& hsg = pl.stage_groups[L];
-        const Group* sg = dgroups + ng * (1 + L);
-        // Per-step segment lists (device copy in stepsegs): item-level list, then one
-        // list per diagonal d in (kLowCut, L].  `active` holds, per item type, the
-        // group positions of the samples whose item is still iterating.
-        std::vector<std::vector<int>> active(its.size());
-        for (size_t k = 0; k < its.size(); ++k) {
-            const Group& G = hsg[its[k].g];
-            active[k].resize(G.count);
-            for (int i = 0; i < G.count; ++i) active[k][i] = pl.perm[G.start + i];
-        }
-        size_t item_seg0 = 0, item_nseg = 0;
-        std::vector<size_t> dseg0(L + 1, 0), dnseg(L + 1, 0);
-        std::vector<double> dpts_pre(L + 1, 0), dpts_post(L + 1, 0);
-        int64_t nitems_active = 0;
-        double item_pts = 0, low_bytes = 0;
-        auto build_lists = [&]() {
-            // sample list
-            std::vector<int64_t> loff(its.size());
-            int64_t nl = 0;
-            item_pts = 0;
-            for (size_t k = 0; k < its.size(); ++k) {
-                loff[k] = nl;
-                for (int s : active[k]) h_list[nl++] = s;
-                item_pts += (double)active[k].size() * pts(its[k].pi, its[k].qi);
-            }
-            nitems_active = nl;
-            size_t ns = 0;
-            int64_t b = 0;
-            item_seg0 = 0;
-            for (size_t k = 0; k < its.size(); ++k) {
-                if (active[k].empty()) continue;
-                const ItemType& it = its[k];
-                h_segs[ns++] = Segment{it.g, it.pi, it.qi, it.pi, it.qi, b, (int64_t)active[k].size(), loff[k],
-                                       it.scr_slot, it.stage_base};
-                b += (int64_t)active[k].size();
-            }
-            item_nseg = ns;
-            // algorithmic bytes of one LOW launch at diagonal min(L, kLowCut)
-            const int dl = std::min(L, kLowCut);
-            low_bytes = 0;
-            for (size_t k = 0; k < its.size(); ++k)
-                for (int pp = 1; pp <= its[k].pi; ++pp)
-                    for (int qq = 1; qq <= its[k].qi; ++qq) {
-                        int dd = pp + qq - 2;
-                        if (dd > dl) continue;
-                        double n = (double)active[k].size() * pts(pp, qq);
-                        low_bytes += n * 2;
-                        if (dd == dl) low_bytes += n * ((pp < its[k].pi && qq < its[k].qi) ? 3 : 2);
-                    }
-            low_bytes *= es;
-            for (int d = kLowCut + 1; d <= L; ++d) {
-                dseg0[d] = ns;
-                b = 0;
-                dpts_pre[d] = dpts_post[d] = 0;
-                for (size_t k = 0; k < its.size(); ++k) {
-                    if (active[k].empty()) continue;
-                    const ItemType& it = its[k];
-                    for (int p = std::max(1, d + 2 - it.qi); p <= std::min(it.pi, d + 1); ++p) {
-                        const int q = d + 2 - p;
-                        h_segs[ns++] = Segment{it.g, it.pi, it.qi, p, q, b, (int64_t)active[k].size(), loff[k],
-                                               it.scr_slot, it.stage_base};
-                        b += (int64_t)active[k].size();
-                        const double n = (double)active[k].size() * pts(p, q);
-                        const double bw = (p < it.pi && q < it.qi) ? 2.0 : 1.0;
-                        const double ch = (p > 1 ? 0.5 : 0.0) + (q > 1 ? 0.5 : 0.0);
-                        dpts_pre[d] += n * (bw + 2 + 1 + ch);  // b, coefficients, u out, restriction out
-                        dpts_post[d] += n * (ch + bw + 2 + 2); // children, b, coefficients, u in/out
-                    }
-                }
-                dnseg[d] = ns - dseg0[d];
-            }
-            MSG_CUDA_TRY(cudaMemcpyAsync(slist, h_list, sizeof(int) * std::max<int64_t>(nl, 1), cudaMemcpyHostToDevice, st));
-            MSG_CUDA_TRY(cudaMemcpyAsync(stepsegs, h_segs, sizeof(Segment) * std::max<size_t>(ns, 1),
-                                         cudaMemcpyHostToDevice, st));
-            return MSG_OK;
-        };
-        auto ctx_of = [&](size_t seg0, size_t n) {
-            DevCtx c = base;
-            c.slist = slist;
-            c.groups = sg;
-            c.segs = stepsegs + seg0;
-            c.nseg = (int)n;
-            return c;
-        };
-        int rc = build_lists();
-        if (rc != MSG_OK) return rc;
-        DevCtx all_items = ctx_of(item_seg0, item_nseg);
-        const int64_t nall = nitems_active;
-        {
-            prof_begin(K_INTERP, st);
-            k_interp<<<(unsigned)nall, kThreads, 0, st>>>(all_items, u64, ax64, ay64);
-            prof_end(K_INTERP, st, item_pts * (8.0 + 16.0 + 8.0), 0.0);
-            MSG_CHECK_LAUNCH();
-        }
-        for (int step = 0;; ++step) {
-            DevCtx ic = ctx_of(item_seg0, item_nseg);
-            MSG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-            prof_begin(K_RESIDUAL, st);
-            k_residual<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, u64, ax64, ay64, sbx, step, prm.max_cycles,
-                                                                       prm.eps, sflag, cyc, rel, stat, counter);
-            prof_end(K_RESIDUAL, st, item_pts * (24.0 + es), 0.0);
-            MSG_CHECK_LAUNCH();
-            MSG_CUDA_TRY(cudaMemcpyAsync(h_counter, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MSG_CUDA_TRY(cudaMemcpyAsync(h_flags, sflag, sizeof(int) * pl.stage_nitems[L], cudaMemcpyDeviceToHost, st));
-            MSG_CUDA_TRY(cudaStreamSynchronize(st));
-            if (*h_counter == 0) break;
-            // keep the items whose flag is set
-            for (size_t k = 0; k < its.size(); ++k) {
-                std::vector<int>& a = active[k];
-                size_t w = 0;
-                for (size_t r = 0; r < a.size(); ++r)
-                    if (h_flags[its[k].stage_base + pl.gpos[a[r]]]) a[w++] = a[r];
-                a.resize(w);
-            }
-            rc = build_lists();
-            if (rc != MSG_OK) return rc;
-            ic = ctx_of(item_seg0, item_nseg);
-            // one mu-cycle (Algorithm 1) of every active item
-            bool launch_err = false;
-            auto launch_low = [&](int d, int calls, int zi) {
-                const size_t shm = sizeof(T) * 4 * kLowNodes * kLowWarps;
-                const unsigned nb = (unsigned)((nitems_active + kLowWarps - 1) / kLowWarps);
-                prof_begin(K_LOW, st);
-                k_low_warp<T><<<nb, kLowWarps * 32, shm, st>>>(ic, nitems_active, su, sbx, sby, ax, ay, d, calls, zi,
-                                                               cp);
-                prof_end(K_LOW, st, low_bytes, 0.0);
-                launch_err |= cudaGetLastError() != cudaSuccess;
-            };
-            auto launch_half = [&](int d, int pre, int zi) {
-                if (dnseg[d] == 0) return;
-                const Segment& last = h_segs[dseg0[d] + dnseg[d] - 1];
-                const int64_t nb = last.blk_start + last.count;
-                DevCtx c = ctx_of(dseg0[d], dnseg[d]);
-                prof_begin(pre ? K_PRE : K_POST, st);
-                if (pre) k_pre<T><<<(unsigned)nb, kThreads, 0, st>>>(c, su, sbx, sby, ax, ay, zi, prm.nu1);
-                else k_post<T><<<(unsigned)nb, kThreads, 0, st>>>(c, su, sbx, sby, ax, ay, prm.nu2, prm.omega);
-                prof_end(pre ? K_PRE : K_POST, st, (pre ? dpts_pre[d] : dpts_post[d]) * es, 0.0);
-                launch_err |= cudaGetLastError() != cudaSuccess;
-            };
-            if (L <= kLowCut) {
-                launch_low(L, 1, 1);
-            } else {
-                struct Frame { int d, k, zi, phase; };
-                std::vector<Frame> stack;
-                stack.push_back({L, 0, 1, 0});
-                while (!stack.empty()) {
-                    Frame& f = stack.back();
-                    if (f.phase == 0) {
-                        launch_half(f.d, 1, f.zi);
-                        f.phase = 1;
-                        if (f.d - 1 <= kLowCut) {
-                            launch_low(f.d - 1, prm.mu, 1);
-                            f.phase = 2;
-                        }
-                        continue;
-                    }
-                    if (f.phase == 1) {
-                        if (f.k < prm.mu) {
-                            int zi = (f.k == 0);
-                            f.k += 1;
-                            stack.push_back({f.d - 1, 0, zi, 0});
-                            continue;
-                        }
-                        f.phase = 2;
-                    }
-                    launch_half(f.d, 0, 0);
-                    stack.pop_back();
-                }
-            }
-            if (launch_err) { set_error("kernel launch failed in the cycle schedule"); return MSG_ERR_CUDA; }
-            prof_begin(K_UPDATE, st);
-            k_update<T><<<(unsigned)nitems_active, kThreads, 0, st>>>(ic, u64, su);
-            prof_end(K_UPDATE, st, item_pts * (16.0 + es), 0.0);
-            MSG_CHECK_LAUNCH();
-        }
-        // QoI of every item of the stage (all samples)
-        for (size_t k = 0; k < its.size(); ++k) {
-            const Group& G = hsg[its[k].g];
-            active[k].resize(G.count);
-            for (int i = 0; i < G.count; ++i) active[k][i] = pl.perm[G.start + i];
-        }
-        rc = build_lists();
-        if (rc != MSG_OK) return rc;
-        prof_begin(K_QOI, st);
-        k_qoi<<<(unsigned)nitems_active, kThreads, 0, st>>>(ctx_of(item_seg0, item_nseg), u64, Z, prm.qoi, Qout);
-        prof_end(K_QOI, st, item_pts * 8.0, 0.0);
-        MSG_CHECK_LAUNCH();
-        MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host lists are rewritten by the next stage
+    // ---- one worker (host thread + stream) per stage
+    const int nst = pl.Lmax + 1;
+    StageQueues Qs;
+    Qs.ready.assign(nst, {});
+    Qs.done.assign(nst, 0);
+    Qs.ready[0] = pl.perm;
+    std::vector<cudaStream_t> streams(nst, nullptr);
+    for (int L = 0; L < nst; ++L) MSG_CUDA_TRY(cudaStreamCreateWithFlags(&streams[L], cudaStreamNonBlocking));
+    std::vector<int> rcs(nst, MSG_OK);
+    std::vector<std::string> errs(nst);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::vector<std::thread> th;
+        for (int L = 0; L < nst; ++L)
+            th.emplace_back([&, L] {
+                cudaSetDevice(dev);
+                rcs[L] = stage_worker<T>(C, L, Qs, streams[L]);
+                if (rcs[L] != MSG_OK) errs[L] = msg_last_error();
+            });
+        for (auto& t : th) t.join();
     }
-    if (cycles_out) MSG_CUDA_TRY(cudaMemcpyAsync(cycles_out, cyc, sizeof(int) * pl.total_q, cudaMemcpyDeviceToDevice, st));
-    if (relres_out) MSG_CUDA_TRY(cudaMemcpyAsync(relres_out, rel, sizeof(double) * pl.total_q, cudaMemcpyDeviceToDevice, st));
+    for (int L = 0; L < nst; ++L) cudaStreamDestroy(streams[L]);
+    for (int L = 0; L < nst; ++L)
+        if (rcs[L] != MSG_OK) { set_error("stage " + std::to_string(L) + ": " + errs[L]); return rcs[L]; }
+
+    // ---- QoI of every grid
+    {
+        DevCtx c = C.base;
+        c.slist = (const int*)(ws + wl.perm);
+        c.groups = C.dgroups;
+        c.segs = (const Segment*)(ws + wl.allsegs);
+        c.nseg = (int)pl.all_segs.size();
+        const int64_t nb = pl.all_segs.empty() ? 0 : pl.all_segs.back().blk_start + pl.all_segs.back().count;
+        prof_begin(K_QOI, st);
+        k_qoi<<<(unsigned)nb, kThreads, 0, st>>>(c, C.u64, Z, prm.qoi, Qout);
+        prof_end(K_QOI, st, (double)pl.total_nodes * 8.0, 0.0);
+        MSG_CHECK_LAUNCH();
+    }
+    if (cycles_out) MSG_CUDA_TRY(cudaMemcpyAsync(cycles_out, C.cyc, sizeof(int) * pl.total_q, cudaMemcpyDeviceToDevice, st));
+    if (relres_out) MSG_CUDA_TRY(cudaMemcpyAsync(relres_out, C.rel, sizeof(double) * pl.total_q, cudaMemcpyDeviceToDevice, st));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));
     return MSG_OK;
 }

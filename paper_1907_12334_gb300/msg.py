@@ -37,7 +37,8 @@ class MsgError(RuntimeError):
 class msg_params(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32),
+                ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32)]
 
 
 @dataclass
@@ -52,10 +53,12 @@ class SolverParams:
     precision: int = MSG_PREC_MIXED
     qoi: int = MSG_QOI_INTEGRAL
     coef: int = MSG_COEF_SERIES
+    tune_block: int = 0      # launch shape only (no effect on results): 0 = library default
+    tune_low_warps: int = 0
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
-                          self.qoi, self.coef)
+                          self.qoi, self.coef, self.tune_block, self.tune_low_warps)
 
 
 _lib = None
