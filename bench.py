@@ -218,7 +218,8 @@ def ours(a, rank, world, local_rank):
         msg.msg_normals(seed, 0, S, M, xi)
         msg.sample_field(prep, npts, M, gemm, xi, Z)
         prm = autotune.tune(PQ, Z.reshape(-1), prm, sample=min(S, 512))
-        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps}
+        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps,
+                 "tune_warp_visit": prm.tune_warp_visit}
 
     def step(k):
         s0 = (k * world + rank) * S

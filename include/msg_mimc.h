@@ -78,6 +78,10 @@ typedef struct {
     int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
     int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 256; multiple of 32) */
     int32_t tune_low_warps; /* launch shape: items per CTA of the warp-resident kernel (0: 4; 1..8) */
+    int32_t tune_warp_visit; /* launch shape: diagonals <= this are visited one warp per grid (0: none beyond the warp-resident ones); 0..24 */
+    int32_t tune_stage_from; /* launch shape: diagonals >= this stage their grid in shared memory when it fits (0: none) */
+    int32_t tune_low_group; /* launch shape: items per warp of the warp-resident kernel (0: 2; 1, 2, 4) */
+    int32_t tune_low_threads; /* launch shape: threads per item there; > 32 puts one item per CTA (0: 32) */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */

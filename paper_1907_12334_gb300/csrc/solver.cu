@@ -25,6 +25,7 @@
 //   su, sbx, sby scratch of the active items' hierarchies: correction e and the
 //                restrictions received from the x-parent and the y-parent.
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -118,6 +119,24 @@ __device__ __forceinline__ TaskRef resolve_at(const DevCtx& cx, int64_t b)
 
 __device__ __forceinline__ TaskRef resolve(const DevCtx& cx) { return resolve_at(cx, blockIdx.x); }
 
+// Task of this block in a 2-D launch: blockIdx.y is the segment, blockIdx.x the
+// sample inside it (direct loads instead of a search; blocks past the
+// segment's count have no task).
+__device__ __forceinline__ bool resolve_2d(const DevCtx& cx, TaskRef& t)
+{
+    const Segment* sg = &cx.segs[blockIdx.y];
+    if ((int64_t)blockIdx.x >= sg->count) return false;
+    const Group& G = cx.groups[sg->g];
+    t.s = cx.slist[sg->list_off + blockIdx.x];
+    t.seg = sg;
+    const int gp = cx.gpos[t.s];
+    t.scr = G.scr_start + (int64_t)gp * G.scr_per_sample + sg->scr_slot;
+    const SampleInfo& S = cx.samples[t.s];
+    t.item = S.q_off + (int64_t)(sg->pi - 1) * S.Q + (sg->qi - 1);
+    t.sidx = sg->stage_base + gp;
+    return true;
+}
+
 // ------------------------------------------------------------ grid ops ----
 
 // 1/x: the correctly rounded FP32 reciprocal in the FP32 cycles (the cycles only
@@ -152,24 +171,38 @@ __device__ __forceinline__ T res_at(const GView<T>& g, int c, int W)
     return b_at(g, c) - Au;
 }
 
+// Thread groups that run one grid operation: a whole CTA (large grids) or one
+// warp (small grids, several tasks per CTA).  `tid` and `n` index the group's
+// threads; sync() orders the group's shared and global memory accesses.
+struct CtaGroup {
+    int tid, n;
+    __device__ CtaGroup() : tid(threadIdx.x), n(blockDim.x) {}
+    __device__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+    int tid, n;
+    __device__ WarpGroup() : tid(threadIdx.x & 31), n(32) {}
+    __device__ void sync() const { __syncwarp(); }
+};
+
 // CTA-wide: zero u on every node, boundary included.  Scratch is reused by
 // hierarchies of other shapes from stage to stage, so a boundary node here may
 // hold an interior value written by an earlier stage.
-template <class T>
-__device__ void cta_zero(const GView<T>& g)
+template <class T, class G>
+__device__ void cta_zero(const G& grp, const GView<T>& g)
 {
     const int n = (g.nx + 1) * (g.ny + 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) g.u[k] = T(0);
+    for (int k = grp.tid; k < n; k += grp.n) g.u[k] = T(0);
 }
 
 // CTA-wide red-black Gauss-Seidel sweeps (red = (i+j) even first).
-template <class T>
-__device__ void cta_smooth(const GView<T>& g, int sweeps)
+template <class T, class G>
+__device__ void cta_smooth(const G& grp, const GView<T>& g, int sweeps)
 {
     const int W = g.nx + 1, half = g.nx >> 1, n = (g.ny - 1) * half;
     for (int sw = 0; sw < sweeps; ++sw)
         for (int colour = 0; colour < 2; ++colour) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            for (int k = grp.tid; k < n; k += grp.n) {
                 int j = 1 + k / half, kk = k % half;
                 int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
                 if (i >= g.nx) continue;
@@ -178,30 +211,30 @@ __device__ void cta_smooth(const GView<T>& g, int sweeps)
                 T nb = (aw * g.u[c - 1] + ae * g.u[c + 1]) + (as * g.u[c - W] + an * g.u[c + W]);
                 g.u[c] = (b_at(g, c) + nb) * rcp_of(aw + ae + as + an);
             }
-            __syncthreads();
+            grp.sync();
         }
 }
 
 // Coarsest grid (1,1): one unknown, v = b / A (Algorithm 1, L = 0).
-template <class T>
-__device__ void cta_coarsest(const GView<T>& g)
+template <class T, class G>
+__device__ void cta_coarsest(const G& grp, const GView<T>& g)
 {
-    if (threadIdx.x < 9) {  // all 3x3 nodes: boundary zeros (see cta_zero) and the unknown
+    if (grp.tid < 9) {  // all 3x3 nodes: boundary zeros (see cta_zero) and the unknown
         const int c = 1 * 3 + 1;
-        g.u[threadIdx.x] = (threadIdx.x == c) ? b_at(g, c) / (g.ax[c - 1] + g.ax[c] + g.ay[c - 3] + g.ay[c]) : T(0);
+        g.u[grp.tid] = (grp.tid == c) ? b_at(g, c) / (g.ax[c - 1] + g.ax[c] + g.ay[c - 3] + g.ay[c]) : T(0);
     }
-    __syncthreads();
+    grp.sync();
 }
 
 // Full-weighting restriction of the residual of g (Eq. (2.3)): R_x r into the
 // x-child's bx (if cxb != nullptr), R_y r into the y-child's by.
-template <class T>
-__device__ void cta_restrict(const GView<T>& g, T* cxb, T* cyb)
+template <class T, class G>
+__device__ void cta_restrict(const G& grp, const GView<T>& g, T* cxb, T* cyb)
 {
     const int W = g.nx + 1;
     if (cxb) {  // child (p-1,q): nx/2 cells, same rows
         const int ncx = g.nx >> 1, Wc = ncx + 1, n = (ncx - 1) * (g.ny - 1);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = grp.tid; k < n; k += grp.n) {
             int ic = 1 + k % (ncx - 1), j = 1 + k / (ncx - 1);
             int c = j * W + 2 * ic;
             T v = T(0.25) * (res_at(g, c - 1, W) + T(2) * res_at(g, c, W) + res_at(g, c + 1, W));
@@ -210,23 +243,23 @@ __device__ void cta_restrict(const GView<T>& g, T* cxb, T* cyb)
     }
     if (cyb) {  // child (p,q-1): same columns, ny/2 cells
         const int ncy = g.ny >> 1, n = (g.nx - 1) * (ncy - 1);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = grp.tid; k < n; k += grp.n) {
             int i = 1 + k % (g.nx - 1), jc = 1 + k / (g.nx - 1);
             int c = 2 * jc * W + i;
             T v = T(0.25) * (res_at(g, c - W, W) + T(2) * res_at(g, c, W) + res_at(g, c + W, W));
             cyb[jc * W + i] = v;
         }
     }
-    __syncthreads();
+    grp.sync();
 }
 
 // Coarse-grid correction (Eq. (2.4) with linear P and the weights of Eq. (2.5)):
 // u += omega * (kx Px e_x + ky Py e_y); one child only when q = 1 or p = 1.
-template <class T>
-__device__ void cta_prolong(const GView<T>& g, const T* ucx, const T* ucy, T omega)
+template <class T, class G>
+__device__ void cta_prolong(const G& grp, const GView<T>& g, const T* ucx, const T* ucy, T omega)
 {
     const int W = g.nx + 1, n = (g.nx - 1) * (g.ny - 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = grp.tid; k < n; k += grp.n) {
         int i = 1 + k % (g.nx - 1), j = 1 + k / (g.nx - 1);
         int c = j * W + i;
         T vx = T(0), vy = T(0);
@@ -248,7 +281,7 @@ __device__ void cta_prolong(const GView<T>& g, const T* ucx, const T* ucy, T ome
         }
         g.u[c] += omega * corr;
     }
-    __syncthreads();
+    grp.sync();
 }
 
 // ------------------------------------------------------- hierarchy views --
@@ -284,27 +317,27 @@ __device__ __forceinline__ GView<T> view_of(const Hier<T>& h, int p, int q)
 }
 
 // Visit halves of Algorithm 1 on one grid (p,q) of an item's hierarchy.
-template <class T>
-__device__ void visit_pre(const Hier<T>& h, int p, int q, int zero_init, int nu1)
+template <class T, class G>
+__device__ void visit_pre(const G& grp, const Hier<T>& h, int p, int q, int zero_init, int nu1)
 {
     GView<T> g = view_of(h, p, q);
-    if (p == 1 && q == 1) { cta_coarsest(g); return; }
-    if (zero_init) { cta_zero(g); __syncthreads(); }
-    cta_smooth(g, nu1);
+    if (p == 1 && q == 1) { cta_coarsest(grp, g); return; }
+    if (zero_init) { cta_zero(grp, g); grp.sync(); }
+    cta_smooth(grp, g, nu1);
     T* cxb = (p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
     T* cyb = (q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    cta_restrict(g, cxb, cyb);
+    cta_restrict(grp, g, cxb, cyb);
 }
 
-template <class T>
-__device__ void visit_post(const Hier<T>& h, int p, int q, int nu2, T omega)
+template <class T, class G>
+__device__ void visit_post(const G& grp, const Hier<T>& h, int p, int q, int nu2, T omega)
 {
     if (p == 1 && q == 1) return;
     GView<T> g = view_of(h, p, q);
     const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
     const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    cta_prolong(g, ucx, ucy, omega);
-    cta_smooth(g, nu2);
+    cta_prolong(grp, g, ucx, ucy, omega);
+    cta_smooth(grp, g, nu2);
 }
 
 struct CycleParams {
@@ -338,17 +371,119 @@ __device__ __forceinline__ Hier<T> hier_of(const DevCtx& cx, const TaskRef& t, T
 template <class T>
 __global__ void k_pre(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
 {
-    TaskRef t = resolve(cx);
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    visit_pre(h, t.seg->p, t.seg->q, zero_init, nu1);
+    visit_pre(CtaGroup(), h, t.seg->p, t.seg->q, zero_init, nu1);
 }
 
 template <class T>
 __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2, double omega)
 {
-    TaskRef t = resolve(cx);
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    visit_post(h, t.seg->p, t.seg->q, nu2, (T)omega);
+    visit_post(CtaGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
+}
+
+// The visit halves with the task's grid staged in shared memory: u, the
+// combined right-hand side and both coefficient arrays are read from global
+// memory once, all sweeps, the residuals of the restriction and the
+// prolongation work on the staged copy, and u is written back once.  Used for
+// grids whose four node arrays fit the launch's dynamic shared memory.
+template <class T>
+__device__ GView<T> stage_grid(const GView<T>& g, bool load_u, T* sm)
+{
+    const int n = (g.nx + 1) * (g.ny + 1);
+    T* su = sm;
+    T* sb = sm + n;
+    T* sax = sm + 2 * n;
+    T* say = sm + 3 * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        su[k] = load_u ? g.u[k] : T(0);
+        sb[k] = b_at(g, k);
+        sax[k] = g.ax[k];
+        say[k] = g.ay[k];
+    }
+    __syncthreads();
+    GView<T> s = g;
+    s.u = su;
+    s.bx = sb;
+    s.by = sb;
+    s.bmode = 0;
+    s.ax = sax;
+    s.ay = say;
+    return s;
+}
+
+template <class T>
+__device__ void unstage_u(const GView<T>& g, const T* su)
+{
+    const int n = (g.nx + 1) * (g.ny + 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) g.u[k] = su[k];
+}
+
+template <class T>
+__global__ void k_pre_s(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    const int p = t.seg->p, q = t.seg->q;
+    const CtaGroup grp;
+    GView<T> g = view_of(h, p, q);
+    if (p == 1 && q == 1) { cta_coarsest(grp, g); return; }
+    GView<T> s = stage_grid(g, !zero_init, (T*)smem_raw);  // zero_init: u starts at 0 (boundary included)
+    cta_smooth(grp, s, nu1);
+    T* cxb = (p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
+    T* cyb = (q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
+    cta_restrict(grp, s, cxb, cyb);
+    unstage_u(g, s.u);
+}
+
+template <class T>
+__global__ void k_post_s(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2, double omega)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    const int p = t.seg->p, q = t.seg->q;
+    if (p == 1 && q == 1) return;
+    const CtaGroup grp;
+    GView<T> g = view_of(h, p, q);
+    GView<T> s = stage_grid(g, true, (T*)smem_raw);
+    const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
+    const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
+    cta_prolong(grp, s, ucx, ucy, (T)omega);
+    cta_smooth(grp, s, nu2);
+    unstage_u(g, s.u);
+}
+
+// The same visit halves with one warp per (item, grid) task, for grids small
+// enough that a CTA per task would leave most of its threads idle and pay CTA
+// barriers for a few hundred points.
+template <class T>
+__global__ void k_pre_w(DevCtx cx, int64_t ntasks, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init,
+                        int nu1)
+{
+    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (task >= ntasks) return;  // whole warps; no block barrier below
+    TaskRef t = resolve_at(cx, task);
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    visit_pre(WarpGroup(), h, t.seg->p, t.seg->q, zero_init, nu1);
+}
+
+template <class T>
+__global__ void k_post_w(DevCtx cx, int64_t ntasks, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2,
+                         double omega)
+{
+    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (task >= ntasks) return;
+    TaskRef t = resolve_at(cx, task);
+    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    visit_post(WarpGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
 // ------------------------------------------------- warp-resident recursion --
@@ -390,13 +525,23 @@ struct WarpLow {
     T* ax;
     T* ay;
     const int (*toff)[kDW + 2];
-    int pi, qi;  // item top (rectangle)
-    int lane;
+    int pi, qi;  // item top (rectangle); 0 for an idle slot of a warp
+    int lane;    // lane inside the item's lane group
+    int ls;      // lanes per item (32 / items per warp)
     __device__ WGrid<T> grid(int p, int q) const
     {
         const int o = toff[p][q];
         return WGrid<T>{u + o, b + o, ax + o, ay + o, 1 << p, 1 << q};
     }
+};
+
+// Barrier of the lanes that share one item: a warp (several items per warp)
+// or a whole CTA (one item on 2-8 warps).
+struct SyncWarp {
+    __device__ static void sync() { __syncwarp(); }
+};
+struct SyncCta {
+    __device__ static void sync() { __syncthreads(); }
 };
 
 template <class T>
@@ -409,7 +554,7 @@ __device__ __forceinline__ T w_res_at(const WGrid<T>& g, int c, int W)
 
 // Red-black sweeps over all grids of diagonal d (grid (p,q) has 2^(p-1) slots
 // per row for each colour; slot kk of row j is node i = first + 2 kk).
-template <class T>
+template <class T, class SY>
 __device__ __forceinline__ void w_sweeps(const WarpLow<T>& w, int d, int plo, int phi, int sweeps)
 {
     for (int sw = 0; sw < sweeps; ++sw)
@@ -418,7 +563,7 @@ __device__ __forceinline__ void w_sweeps(const WarpLow<T>& w, int d, int plo, in
                 const int q = d + 2 - p;
                 WGrid<T> g = w.grid(p, q);
                 const int W = g.nx + 1, sh = p - 1, n = (g.ny - 1) << sh;
-                for (int k = w.lane; k < n; k += 32) {
+                for (int k = w.lane; k < n; k += w.ls) {
                     const int j = 1 + (k >> sh), kk = k & ((1 << sh) - 1);
                     const int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
                     if (i >= g.nx) continue;
@@ -428,17 +573,17 @@ __device__ __forceinline__ void w_sweeps(const WarpLow<T>& w, int d, int plo, in
                     g.u[c] = (g.b[c] + nb) * rcp_of(aw + ae + as + an);
                 }
             }
-            __syncwarp();
+            SY::sync();
         }
 }
 
-template <class T, int D>
+template <class T, class SY, int D>
 __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu1)
 {
     if constexpr (D == 0) {
         WGrid<T> g = w.grid(1, 1);
-        if (w.lane == 0) g.u[4] = g.b[4] * rcp_of(g.ax[3] + g.ax[4] + g.ay[1] + g.ay[4]);
-        __syncwarp();
+        if (w.lane == 0 && w.pi > 0) g.u[4] = g.b[4] * rcp_of(g.ax[3] + g.ax[4] + g.ay[1] + g.ay[4]);
+        SY::sync();
     } else {
         int plo, phi;
         diag_range(D, w.pi, w.qi, plo, phi);
@@ -446,11 +591,11 @@ __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu
             for (int p = plo; p <= phi; ++p) {
                 WGrid<T> g = w.grid(p, D + 2 - p);
                 const int n = (g.nx + 1) * (g.ny + 1);
-                for (int k = w.lane; k < n; k += 32) g.u[k] = T(0);
+                for (int k = w.lane; k < n; k += w.ls) g.u[k] = T(0);
             }
-            __syncwarp();
+            SY::sync();
         }
-        w_sweeps(w, D, plo, phi, nu1);
+        w_sweeps<T, SY>(w, D, plo, phi, nu1);
         // restriction (Eq. (2.3)) in two passes: x-children are set, y-children are
         // set or completed, so a two-parent child gets R_x/2 + R_y/2
         for (int p = max(plo, 2); p <= phi; ++p) {
@@ -459,7 +604,7 @@ __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu
             WGrid<T> c = w.grid(p - 1, q);
             const T wgt = (q < w.qi) ? T(0.5) : T(1);
             const int W = g.nx + 1, shc = p - 1, Wc = (1 << shc) + 1, n = (g.ny - 1) << shc;
-            for (int k = w.lane; k < n; k += 32) {
+            for (int k = w.lane; k < n; k += w.ls) {
                 const int ic = k & ((1 << shc) - 1), j = 1 + (k >> shc);
                 if (ic == 0) continue;
                 const int cc = j * W + 2 * ic;
@@ -467,7 +612,7 @@ __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu
                 c.b[j * Wc + ic] = wgt * v;
             }
         }
-        __syncwarp();
+        SY::sync();
         for (int p = plo; p <= phi; ++p) {
             const int q = D + 2 - p;
             if (q < 2) continue;
@@ -475,7 +620,7 @@ __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu
             WGrid<T> c = w.grid(p, q - 1);
             const bool both = p < w.pi;  // child (p, q-1) also has the x-parent (p+1, q-1)
             const int W = g.nx + 1, n = ((g.ny >> 1) - 1) << p;
-            for (int k = w.lane; k < n; k += 32) {
+            for (int k = w.lane; k < n; k += w.ls) {
                 const int i = k & (g.nx - 1), jc = 1 + (k >> p);
                 if (i == 0) continue;
                 const int cc = 2 * jc * W + i;
@@ -484,11 +629,11 @@ __device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu
                 else c.b[jc * W + i] = v;
             }
         }
-        __syncwarp();
+        SY::sync();
     }
 }
 
-template <class T, int D>
+template <class T, class SY, int D>
 __device__ __forceinline__ void w_post(const WarpLow<T>& w, int nu2, T omega)
 {
     int plo, phi;
@@ -499,7 +644,7 @@ __device__ __forceinline__ void w_post(const WarpLow<T>& w, int nu2, T omega)
         const T* ucx = (p > 1) ? w.grid(p - 1, q).u : nullptr;
         const T* ucy = (q > 1) ? w.grid(p, q - 1).u : nullptr;
         const int W = g.nx + 1, n = (g.ny - 1) << p;
-        for (int k = w.lane; k < n; k += 32) {
+        for (int k = w.lane; k < n; k += w.ls) {
             const int i = k & (g.nx - 1), j = 1 + (k >> p);
             if (i == 0) continue;
             const int c = j * W + i;
@@ -523,42 +668,45 @@ __device__ __forceinline__ void w_post(const WarpLow<T>& w, int nu2, T omega)
             g.u[c] += omega * corr;
         }
     }
-    __syncwarp();
-    w_sweeps(w, D, plo, phi, nu2);
+    SY::sync();
+    w_sweeps<T, SY>(w, D, plo, phi, nu2);
 }
 
 // One mu-cycle of Algorithm 1 at diagonal D, unrolled at compile time.
-template <class T, int D>
+template <class T, class SY, int D>
 __device__ void w_cycle(const WarpLow<T>& w, int zero_init, const CycleParams& cp)
 {
-    w_pre<T, D>(w, zero_init, cp.nu1);
+    w_pre<T, SY, D>(w, zero_init, cp.nu1);
     if constexpr (D > 0) {
-        for (int k = 0; k < cp.mu; ++k) w_cycle<T, D - 1>(w, k == 0, cp);
-        w_post<T, D>(w, cp.nu2, (T)cp.omega);
+        for (int k = 0; k < cp.mu; ++k) w_cycle<T, SY, D - 1>(w, k == 0, cp);
+        w_post<T, SY, D>(w, cp.nu2, (T)cp.omega);
     }
 }
 
-template <class T>
+template <class T, class SY>
 __device__ void w_mu_cycle(const WarpLow<T>& w, int d, int zero_init, const CycleParams& cp)
 {
     static_assert(kDW == 4, "dispatch below covers diagonals 0..4");
     switch (d) {
-    case 0: w_cycle<T, 0>(w, zero_init, cp); break;
-    case 1: w_cycle<T, 1>(w, zero_init, cp); break;
-    case 2: w_cycle<T, 2>(w, zero_init, cp); break;
-    case 3: w_cycle<T, 3>(w, zero_init, cp); break;
-    default: w_cycle<T, 4>(w, zero_init, cp); break;
+    case 0: w_cycle<T, SY, 0>(w, zero_init, cp); break;
+    case 1: w_cycle<T, SY, 1>(w, zero_init, cp); break;
+    case 2: w_cycle<T, SY, 2>(w, zero_init, cp); break;
+    case 3: w_cycle<T, SY, 3>(w, zero_init, cp); break;
+    default: w_cycle<T, SY, 4>(w, zero_init, cp); break;
     }
 }
 
-// `calls` mu-cycles at diagonal dl <= kDW of each item, one warp per item.
+// `calls` mu-cycles at diagonal dl <= kDW of each item.  A warp carries
+// `group` items (1, 2 or 4), each on 32/group lanes, in lockstep: all items of
+// a launch run the same sequence of phases (same dl, mu, nu), so the warp
+// barriers line up and one instruction stream serves several items.
 // Reads the coefficients of the item's grids with d <= dl and the right-hand
 // side of its diagonal-dl grids (combined from the parents' restrictions, or
 // the item's own residual when dl is its top); writes back u of diagonal dl.
-template <class T>
-__global__ void __launch_bounds__(kLowWarpsMax * 32) k_low_warp(DevCtx cx, int64_t nitems, T* su, const T* sbx,
-                                                            const T* sby, const T* ax, const T* ay, int dl,
-                                                            int calls, int zero_init, CycleParams cp)
+template <class T, class SY>
+__global__ void __launch_bounds__(256) k_low_warp(DevCtx cx, int64_t nitems, int group, T* su,
+                                                            const T* sbx, const T* sby, const T* ax, const T* ay,
+                                                            int dl, int calls, int zero_init, CycleParams cp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int toff[kDW + 2][kDW + 2];
@@ -571,34 +719,46 @@ __global__ void __launch_bounds__(kLowWarpsMax * 32) k_low_warp(DevCtx cx, int64
             }
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (it >= nitems) return;  // no block-wide barrier below this point
-    const TaskRef t = resolve_at(cx, it);
-    const SampleInfo& S = cx.samples[t.s];
+    // SyncWarp: `group` items per warp; SyncCta: one item per CTA on all its threads
+    const bool cta = std::is_same<SY, SyncCta>::value;
+    const int warp = cta ? 0 : (threadIdx.x >> 5), lane = cta ? threadIdx.x : (threadIdx.x & 31);
+    const int ls = cta ? (int)blockDim.x : 32 / group, sub = lane / ls, sl = lane % ls;
+    const int64_t first = cta ? (int64_t)blockIdx.x : ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * group;
+    if (first >= nitems) return;  // whole warp idle; no block-wide barrier below this point
+    const int64_t it = first + sub;
+    const bool valid = it < nitems;
     WarpLow<T> w;
-    T* base = (T*)smem_raw + (size_t)warp * 4 * kLowNodes;
+    T* base = (T*)smem_raw + (size_t)(cta ? 0 : warp * group + sub) * 4 * kLowNodes;
     w.u = base;
     w.b = base + kLowNodes;
     w.ax = base + 2 * kLowNodes;
     w.ay = base + 3 * kLowNodes;
     w.toff = toff;
-    w.pi = t.seg->pi;
-    w.qi = t.seg->qi;
-    w.lane = lane;
-    for (int k = lane; k < kLowNodes; k += 32) w.u[k] = T(0);
+    w.lane = sl;
+    w.ls = ls;
+    TaskRef t{};
+    const SampleInfo* S = nullptr;
+    if (valid) {
+        t = resolve_at(cx, it);
+        S = &cx.samples[t.s];
+        w.pi = t.seg->pi;
+        w.qi = t.seg->qi;
+    } else {
+        w.pi = w.qi = 0;  // no grids: the slot follows the phases without work
+    }
+    for (int k = sl; k < kLowNodes; k += ls) w.u[k] = T(0);
     for (int p = 1; p <= min(w.pi, dl + 1); ++p)
         for (int q = 1; q <= min(w.qi, dl + 2 - p); ++q) {
             const int n = low_nodes(p, q), o = toff[p][q];
-            const int64_t co = S.node_off + grid_offset(p, q, S.Q);
-            for (int k = lane; k < n; k += 32) {
+            const int64_t co = S->node_off + grid_offset(p, q, S->Q);
+            for (int k = sl; k < n; k += ls) {
                 w.ax[o + k] = ax[co + k];
                 w.ay[o + k] = ay[co + k];
             }
             if (p + q - 2 == dl) {
                 const int64_t so = t.scr + grid_offset(p, q, w.qi);
                 const bool hx = p < w.pi, hy = q < w.qi;
-                for (int k = lane; k < n; k += 32) {
+                for (int k = sl; k < n; k += ls) {
                     T v;
                     if (hx && hy) v = T(0.5) * sbx[so + k] + T(0.5) * sby[so + k];
                     else if (hy) v = sby[so + k];
@@ -607,14 +767,15 @@ __global__ void __launch_bounds__(kLowWarpsMax * 32) k_low_warp(DevCtx cx, int64
                 }
             }
         }
-    __syncwarp();
-    for (int c = 0; c < calls; ++c) w_mu_cycle(w, dl, c == 0 ? zero_init : 0, cp);
+    SY::sync();
+    for (int c = 0; c < calls; ++c) w_mu_cycle<T, SY>(w, dl, c == 0 ? zero_init : 0, cp);
+    if (!valid) return;
     int plo, phi;
     diag_range(dl, w.pi, w.qi, plo, phi);
     for (int p = plo; p <= phi; ++p) {
         const int q = dl + 2 - p, n = low_nodes(p, q), o = toff[p][q];
         T* dst = su + t.scr + grid_offset(p, q, w.qi);
-        for (int k = lane; k < n; k += 32) dst[k] = w.u[o + k];
+        for (int k = sl; k < n; k += ls) dst[k] = w.u[o + k];
     }
 }
 
@@ -888,6 +1049,19 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         set_error("tune_block must be 0 or a multiple of 32 in [32, 1024]");
         return MSG_ERR_INVALID;
     }
+    if (prm->tune_low_threads != 0 && (prm->tune_low_threads < 32 || prm->tune_low_threads > 256 ||
+                                       prm->tune_low_threads % 32)) {
+        set_error("tune_low_threads must be 0 or a multiple of 32 in [32, 256]");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->tune_low_group != 0 && prm->tune_low_group != 1 && prm->tune_low_group != 2 && prm->tune_low_group != 4) {
+        set_error("tune_low_group must be 0, 1, 2 or 4");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->tune_stage_from < 0 || prm->tune_warp_visit < 0 || prm->tune_warp_visit > 24) {
+        set_error("tune_warp_visit must be in [0, 24]");
+        return MSG_ERR_INVALID;
+    }
     if (prm->tune_low_warps < 0 || prm->tune_low_warps > kLowWarpsMax) {
         set_error("tune_low_warps must be in [0, 8]");
         return MSG_ERR_INVALID;
@@ -1035,6 +1209,7 @@ WsLayout layout_of(const Plan& pl, int precision)
 }
 
 constexpr int kThreads = 256;
+constexpr size_t kStageSmemMax = 200 * 1024;  // grids staged in shared memory up to this many bytes
 constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-resident, one launch
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
@@ -1083,6 +1258,10 @@ struct SolveCtx {
     CycleParams cp;
     int block;      // threads per CTA of the PRE/POST visit kernels
     int low_warps;  // items (warps) per CTA of the warp-resident kernel
+    int warp_visit_max;  // diagonals up to this one are visited with one warp per task
+    int stage_from;      // diagonals from this one on are staged in shared memory when they fit
+    int low_group;       // items per warp in the warp-resident kernel
+    int low_threads;     // > 32: one item per CTA of this many threads
 };
 
 // Stage L of FMSG for the samples handed over by stage L-1: cubic
@@ -1229,6 +1408,9 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         std::vector<int> admitted;
         {
             std::unique_lock<std::mutex> lk(Qs.mu);
+            // MSG_SERIAL_STAGES=1 (diagnostics): stage L starts only once stage L-1 is finished
+            static const bool serial = getenv("MSG_SERIAL_STAGES") != nullptr;
+            if (serial && L > 0) Qs.cv.wait(lk, [&] { return Qs.abort || Qs.done[L - 1]; });
             if (open_items == 0)
                 Qs.cv.wait(lk, [&] { return Qs.abort || !Qs.ready[L].empty() || (L == 0 || Qs.done[L - 1]); });
             if (Qs.abort) return finish(MSG_OK);
@@ -1311,11 +1493,19 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         DevCtx ic = ctx_of(0, item_nseg);
         bool launch_err = false;
         auto launch_low = [&](int d, int calls, int zi) {
-            const int lw = C.low_warps;
-            const size_t shm = sizeof(T) * 4 * kLowNodes * lw;
-            const unsigned nb = (unsigned)((nitems + lw - 1) / lw);
             prof_begin(K_LOW, st);
-            k_low_warp<T><<<nb, lw * 32, shm, st>>>(ic, nitems, su, sbx, sby, C.ax, C.ay, d, calls, zi, C.cp);
+            if (C.low_threads > 32) {  // one item per CTA
+                const size_t shm = sizeof(T) * 4 * kLowNodes;
+                k_low_warp<T, SyncCta><<<(unsigned)nitems, C.low_threads, shm, st>>>(ic, nitems, 1, su, sbx, sby, C.ax,
+                                                                                   C.ay, d, calls, zi, C.cp);
+            } else {
+                const int lw = C.low_warps, gi = C.low_group;
+                const size_t shm = sizeof(T) * 4 * kLowNodes * lw * gi;
+                const int64_t per_cta = (int64_t)lw * gi;
+                const unsigned nb = (unsigned)((nitems + per_cta - 1) / per_cta);
+                k_low_warp<T, SyncWarp><<<nb, lw * 32, shm, st>>>(ic, nitems, gi, su, sbx, sby, C.ax, C.ay, d, calls,
+                                                                  zi, C.cp);
+            }
             prof_end(K_LOW, st, low_bytes, 0.0);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
@@ -1324,9 +1514,28 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             const Segment& last = h_segs[dseg0[d] + dnseg[d] - 1];
             const int64_t nb = last.blk_start + last.count;
             DevCtx c = ctx_of(dseg0[d], dnseg[d]);
+            // largest grid of this diagonal among the launch's tasks: staged in shared memory if it fits
+            int64_t maxn = 0;
+            for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k)
+                maxn = std::max<int64_t>(maxn, (int64_t)((1 << h_segs[k].p) + 1) * ((1 << h_segs[k].q) + 1));
+            const size_t shm = sizeof(T) * 4 * (size_t)maxn;
             prof_begin(pre ? K_PRE : K_POST, st);
-            if (pre) k_pre<T><<<(unsigned)nb, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
-            else k_post<T><<<(unsigned)nb, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+            int64_t maxc = 0;
+            for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k) maxc = std::max<int64_t>(maxc, h_segs[k].count);
+            const dim3 g2((unsigned)maxc, (unsigned)dnseg[d]);  // x: sample in segment, y: segment
+            if (d >= C.stage_from && shm <= kStageSmemMax) {  // CTA per task, grid staged in shared memory
+                if (pre) k_pre_s<T><<<g2, C.block, shm, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+                else k_post_s<T><<<g2, C.block, shm, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+            } else if (d <= C.warp_visit_max) {  // one warp per task
+                const int wpb = 8;
+                const unsigned g = (unsigned)((nb + wpb - 1) / wpb);
+                if (pre) k_pre_w<T><<<g, wpb * 32, 0, st>>>(c, nb, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+                else k_post_w<T><<<g, wpb * 32, 0, st>>>(c, nb, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+            } else if (pre) {
+                k_pre<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+            } else {
+                k_post<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+            }
             prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
@@ -1388,7 +1597,9 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
                   (const double*)(ws + wl.ax64), (const double*)(ws + wl.ay64), nullptr, nullptr,
                   (int*)(ws + wl.nstep), (int*)(ws + wl.cycles_i), (double*)(ws + wl.relres_i),
                   CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kThreads,
-                  prm.tune_low_warps ? prm.tune_low_warps : 4};
+                  prm.tune_low_warps ? prm.tune_low_warps : 4, prm.tune_warp_visit ? prm.tune_warp_visit : kDW,
+                  prm.tune_stage_from ? prm.tune_stage_from : 99, prm.tune_low_group ? prm.tune_low_group : 2,
+                  prm.tune_low_threads ? prm.tune_low_threads : 32};
     float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
     float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
     C.ax = mixed ? (const T*)ax32 : (const T*)(ws + wl.ax64);
@@ -1414,8 +1625,16 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes * kLowWarpsMax)));
+    if (sizeof(T) * 4 * kLowNodes * C.low_warps * C.low_group > kStageSmemMax + 24 * 1024) {
+        set_error("tune_low_warps * tune_low_group items do not fit the shared memory of one CTA");
+        return MSG_ERR_INVALID;
+    }
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T, SyncWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * 4 * kLowNodes * C.low_warps * C.low_group)));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T, SyncCta>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * 4 * kLowNodes)));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_post_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- one worker (host thread + stream) per stage

@@ -38,7 +38,9 @@ class msg_params(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32),
-                ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32)]
+                ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32),
+                ("tune_warp_visit", ctypes.c_int32), ("tune_stage_from", ctypes.c_int32),
+                ("tune_low_group", ctypes.c_int32), ("tune_low_threads", ctypes.c_int32)]
 
 
 @dataclass
@@ -55,10 +57,15 @@ class SolverParams:
     coef: int = MSG_COEF_SERIES
     tune_block: int = 0      # launch shape only (no effect on results): 0 = library default
     tune_low_warps: int = 0
+    tune_warp_visit: int = 0
+    tune_stage_from: int = 0
+    tune_low_group: int = 0
+    tune_low_threads: int = 0
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
-                          self.qoi, self.coef, self.tune_block, self.tune_low_warps)
+                          self.qoi, self.coef, self.tune_block, self.tune_low_warps, self.tune_warp_visit,
+                          self.tune_stage_from, self.tune_low_group, self.tune_low_threads)
 
 
 _lib = None
