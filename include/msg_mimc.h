@@ -69,7 +69,7 @@ extern "C" {
  * adaptive nu_0 until ||r||/||b|| <= eps on each grid). */
 typedef struct {
     int32_t mu;         /* 1 = V-cycle, 2 = W-cycle */
-    int32_t nu1, nu2;   /* pre- and post-smoothing sweeps */
+    int32_t nu1, nu2;   /* pre- and post-smoothing sweeps, 0..64 each, nu1 + nu2 >= 1 */
     int32_t max_cycles; /* cap on cycles per grid */
     double eps;         /* relative residual target per grid */
     double omega;       /* damping of the coarse-grid correction */
@@ -77,11 +77,10 @@ typedef struct {
     int32_t qoi;        /* MSG_QOI_* */
     int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
     int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 256; multiple of 32) */
-    int32_t tune_low_warps; /* launch shape: items per CTA of the warp-resident kernel (0: 4; 1..8) */
+    int32_t tune_low_warps; /* launch shape: items per CTA of the low-diagonal kernel at one warp per item (0: 2; 1..8) */
     int32_t tune_warp_visit; /* launch shape: diagonals <= this are visited one warp per grid (0: none beyond the warp-resident ones); 0..24 */
     int32_t tune_stage_from; /* launch shape: diagonals >= this stage their grid in shared memory when it fits (0: none) */
-    int32_t tune_low_group; /* launch shape: items per warp of the warp-resident kernel (0: 2; 1, 2, 4) */
-    int32_t tune_low_threads; /* launch shape: threads per item there; > 32 puts one item per CTA (0: 32) */
+    int32_t tune_low_threads; /* launch shape: threads per item there: 32, or 64/128 for one item per CTA (0: 32) */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */

@@ -199,12 +199,13 @@ __device__ void cta_zero(const G& grp, const GView<T>& g)
 template <class T, class G>
 __device__ void cta_smooth(const G& grp, const GView<T>& g, int sweeps)
 {
-    const int W = g.nx + 1, half = g.nx >> 1, n = (g.ny - 1) * half;
+    // slot kk of row j of a colour is node i = first + 2 kk; nx/2 = 2^sh slots per row
+    const int W = g.nx + 1, sh = __ffs(g.nx) - 2, n = (g.ny - 1) << sh;
     for (int sw = 0; sw < sweeps; ++sw)
         for (int colour = 0; colour < 2; ++colour) {
             for (int k = grp.tid; k < n; k += grp.n) {
-                int j = 1 + k / half, kk = k % half;
-                int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
+                const int j = 1 + (k >> sh), kk = k & ((1 << sh) - 1);
+                const int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
                 if (i >= g.nx) continue;
                 int c = j * W + i;
                 T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
@@ -232,20 +233,22 @@ template <class T, class G>
 __device__ void cta_restrict(const G& grp, const GView<T>& g, T* cxb, T* cyb)
 {
     const int W = g.nx + 1;
-    if (cxb) {  // child (p-1,q): nx/2 cells, same rows
-        const int ncx = g.nx >> 1, Wc = ncx + 1, n = (ncx - 1) * (g.ny - 1);
+    if (cxb) {  // child (p-1,q): nx/2 = 2^shc cells, same rows (slot ic = 0 is the boundary)
+        const int ncx = g.nx >> 1, Wc = ncx + 1, shc = __ffs(ncx) - 1, n = (g.ny - 1) << shc;
         for (int k = grp.tid; k < n; k += grp.n) {
-            int ic = 1 + k % (ncx - 1), j = 1 + k / (ncx - 1);
-            int c = j * W + 2 * ic;
+            const int ic = k & (ncx - 1), j = 1 + (k >> shc);
+            if (ic == 0) continue;
+            const int c = j * W + 2 * ic;
             T v = T(0.25) * (res_at(g, c - 1, W) + T(2) * res_at(g, c, W) + res_at(g, c + 1, W));
             cxb[j * Wc + ic] = v;
         }
     }
-    if (cyb) {  // child (p,q-1): same columns, ny/2 cells
-        const int ncy = g.ny >> 1, n = (g.nx - 1) * (ncy - 1);
+    if (cyb) {  // child (p,q-1): same columns, ny/2 cells (slot i = 0 is the boundary)
+        const int ncy = g.ny >> 1, sh = __ffs(g.nx) - 1, n = (ncy - 1) << sh;
         for (int k = grp.tid; k < n; k += grp.n) {
-            int i = 1 + k % (g.nx - 1), jc = 1 + k / (g.nx - 1);
-            int c = 2 * jc * W + i;
+            const int i = k & (g.nx - 1), jc = 1 + (k >> sh);
+            if (i == 0) continue;
+            const int c = 2 * jc * W + i;
             T v = T(0.25) * (res_at(g, c - W, W) + T(2) * res_at(g, c, W) + res_at(g, c + W, W));
             cyb[jc * W + i] = v;
         }
@@ -258,10 +261,11 @@ __device__ void cta_restrict(const G& grp, const GView<T>& g, T* cxb, T* cyb)
 template <class T, class G>
 __device__ void cta_prolong(const G& grp, const GView<T>& g, const T* ucx, const T* ucy, T omega)
 {
-    const int W = g.nx + 1, n = (g.nx - 1) * (g.ny - 1);
+    const int W = g.nx + 1, sh = __ffs(g.nx) - 1, n = (g.ny - 1) << sh;
     for (int k = grp.tid; k < n; k += grp.n) {
-        int i = 1 + k % (g.nx - 1), j = 1 + k / (g.nx - 1);
-        int c = j * W + i;
+        const int i = k & (g.nx - 1), j = 1 + (k >> sh);  // slot i = 0 is the boundary
+        if (i == 0) continue;
+        const int c = j * W + i;
         T vx = T(0), vy = T(0);
         if (ucx) {
             const int Wc = (g.nx >> 1) + 1, r = j * Wc + (i >> 1);
@@ -486,18 +490,27 @@ __global__ void k_post_w(DevCtx cx, int64_t ntasks, T* su, T* sbx, T* sby, const
     visit_post(WarpGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
-// ------------------------------------------------- warp-resident recursion --
+// ---------------------------------------------- table-driven low diagonals --
 //
 // Diagonals d <= kDW of an item's hierarchy are visited 2^(L-d) times per
 // cycle (Algorithm 1 with mu = 2) but hold only a few hundred unknowns, so
-// their cost is the latency of the dependent phases, not bandwidth.  One warp
-// owns one item: u, b and the two face-coefficient arrays of every grid with
-// p + q <= kDW + 2 live in shared memory (padded node layout, triangle order
-// p major), all grids of a diagonal advance together in one phase, and phases
-// are separated by __syncwarp only.
+// their cost is the latency of the dependent phases, not bandwidth.  One
+// thread group (a warp, or a CTA of 64/128 threads) owns one item: u, b and
+// the two face-coefficient arrays of every grid with p + q <= kDW + 2 live in
+// shared memory as four planes of the same node layout (grids ordered by
+// diagonal), and the mu-cycles run as a flat program of phases.
+//
+// The program is the recursion of Algorithm 1 unrolled on the host: a list
+// of (phase kind, diagonal) words.  What a phase touches is a table of node
+// entries of its (kind, diagonal) for the item's class; the class is the
+// clipped shape of the triangle, (min(pi, dl+1), min(qi, dl+1), dl), which
+// fixes the grids present and the restriction weights.  Phases are separated
+// by the group's barrier only.
 
 constexpr int kDW = 4;
-constexpr int kLowWarpsMax = 8;  // warps (items) per CTA of the warp-resident kernel: 1..8, default 4
+constexpr int kLowWarpsMax = 8;  // items per CTA of the one-warp-per-item variant: 1..8
+constexpr int kLowGrids = (kDW + 1) * (kDW + 2) / 2;
+constexpr int kLowClasses = 55;  // sum over dl = 0..kDW of (dl + 1)^2
 
 __host__ __device__ constexpr int low_nodes(int p, int q) { return ((1 << p) + 1) * ((1 << q) + 1); }
 __host__ __device__ constexpr int low_total()
@@ -509,273 +522,191 @@ __host__ __device__ constexpr int low_total()
 }
 constexpr int kLowNodes = low_total();
 
-template <class T>
-struct WGrid {
-    T* u;
-    T* b;
-    const T* ax;
-    const T* ay;
-    int nx, ny;
-};
+// phase kinds; a program word is kind | diagonal << 3, a resolved program
+// word (per class, empty phases dropped) is {kind | entries << 3, first entry}
+enum LowKind { LK_SMOOTH_RED = 0, LK_SMOOTH_BLACK, LK_RX, LK_RY, LK_PROL, LK_ZERO, LK_NKIND };
 
-template <class T>
-struct WarpLow {
-    T* u;
-    T* b;
-    T* ax;
-    T* ay;
-    const int (*toff)[kDW + 2];
-    int pi, qi;  // item top (rectangle); 0 for an idle slot of a warp
-    int lane;    // lane inside the item's lane group
-    int ls;      // lanes per item (32 / items per warp)
-    __device__ WGrid<T> grid(int p, int q) const
-    {
-        const int o = toff[p][q];
-        return WGrid<T>{u + o, b + o, ax + o, ay + o, 1 << p, 1 << q};
-    }
-};
-
-// Barrier of the lanes that share one item: a warp (several items per warp)
-// or a whole CTA (one item on 2-8 warps).
-struct SyncWarp {
-    __device__ static void sync() { __syncwarp(); }
-};
-struct SyncCta {
-    __device__ static void sync() { __syncthreads(); }
-};
-
-template <class T>
-__device__ __forceinline__ T w_res_at(const WGrid<T>& g, int c, int W)
+// Shape class of the triangle below diagonal dl of an item (pic, qic in 1..dl+1).
+__host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
 {
-    T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
-    T Au = (aw + ae + as + an) * g.u[c] - (aw * g.u[c - 1] + ae * g.u[c + 1]) - (as * g.u[c - W] + an * g.u[c + W]);
-    return g.b[c] - Au;
+    return dl * (dl + 1) * (2 * dl + 1) / 6 + (pic - 1) * (dl + 1) + (qic - 1);
 }
 
-// Red-black sweeps over all grids of diagonal d (grid (p,q) has 2^(p-1) slots
-// per row for each colour; slot kk of row j is node i = first + 2 kk).
-template <class T, class SY>
-__device__ __forceinline__ void w_sweeps(const WarpLow<T>& w, int d, int plo, int phi, int sweeps)
+struct LowDesc {
+    int nn;                       // nodes of the class's grids: the size of each plane
+    int dl;
+    int prog, nops;               // resolved program of the class (set per solve)
+    int ngrid;
+    int grid[kLowGrids];          // p | q << 4 | first node << 8, ordered by diagonal
+    int cnt[kDW + 1][LK_NKIND];   // entries of each (diagonal, kind); LK_ZERO: nodes
+    int off[kDW + 1][LK_NKIND];   // first entry in the table blob; LK_ZERO: first node
+};
+
+// Table entries (uint2):
+//   smooth  x = c | W << 16                     node c of a grid with row stride W
+//   RX, RY  x = child c | parent c << 16,  y = W | flag << 16
+//           RX: child b = R_x r (flag: halved, the child has a y-parent too)
+//           RY: child b = R_y r (flag: b += R_y r / 2, the child has an x-parent)
+//   prolong x = c | W << 12 | i odd << 20 | j odd << 21 | has x-child << 22 | has y-child << 23
+//           y = x-child node | y-child node << 16 (the coarse node left of / below (i,j))
+
+template <class T>
+__device__ __forceinline__ T low_res(const T* u, const T* b, const T* fx, const T* fy, int c, int W)
 {
-    for (int sw = 0; sw < sweeps; ++sw)
-        for (int colour = 0; colour < 2; ++colour) {
-            for (int p = plo; p <= phi; ++p) {
-                const int q = d + 2 - p;
-                WGrid<T> g = w.grid(p, q);
-                const int W = g.nx + 1, sh = p - 1, n = (g.ny - 1) << sh;
-                for (int k = w.lane; k < n; k += w.ls) {
-                    const int j = 1 + (k >> sh), kk = k & ((1 << sh) - 1);
-                    const int i = (((1 + j) & 1) == colour ? 1 : 2) + 2 * kk;
-                    if (i >= g.nx) continue;
-                    const int c = j * W + i;
-                    T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
-                    T nb = (aw * g.u[c - 1] + ae * g.u[c + 1]) + (as * g.u[c - W] + an * g.u[c + W]);
-                    g.u[c] = (g.b[c] + nb) * rcp_of(aw + ae + as + an);
-                }
-            }
-            SY::sync();
-        }
+    T aw = fx[c - 1], ae = fx[c], as = fy[c - W], an = fy[c];
+    T Au = (aw + ae + as + an) * u[c] - (aw * u[c - 1] + ae * u[c + 1]) - (as * u[c - W] + an * u[c + W]);
+    return b[c] - Au;
 }
 
-template <class T, class SY, int D>
-__device__ __forceinline__ void w_pre(const WarpLow<T>& w, int zero_init, int nu1)
+// first entry of a phase for this lane (none for zeroing, or past the count)
+__device__ __forceinline__ uint2 low_first(const uint2* ent, uint2 op, int tid)
 {
-    if constexpr (D == 0) {
-        WGrid<T> g = w.grid(1, 1);
-        if (w.lane == 0 && w.pi > 0) g.u[4] = g.b[4] * rcp_of(g.ax[3] + g.ax[4] + g.ay[1] + g.ay[4]);
-        SY::sync();
+    const int kind = op.x & 7, cnt = (int)(op.x >> 3);
+    return (kind != LK_ZERO && tid < cnt) ? ent[op.y + tid] : make_uint2(0u, 0u);
+}
+
+template <class T>
+__device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint2 e)
+{
+    const int c = e.x & 0xFFFF, W = e.x >> 16;
+    T aw = fx[c - 1], ae = fx[c], as = fy[c - W], an = fy[c];
+    T nb = (aw * u[c - 1] + ae * u[c + 1]) + (as * u[c - W] + an * u[c + W]);
+    u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
+}
+
+template <class T>
+__device__ __forceinline__ void low_rx(const T* u, T* b, const T* fx, const T* fy, uint2 e)
+{
+    const int cc = e.x & 0xFFFF, pc = e.x >> 16, W = e.y & 0xFFFF;
+    T v = T(0.25) * (low_res(u, b, fx, fy, pc - 1, W) + T(2) * low_res(u, b, fx, fy, pc, W) +
+                     low_res(u, b, fx, fy, pc + 1, W));
+    b[cc] = (e.y >> 16) ? T(0.5) * v : v;
+}
+
+template <class T>
+__device__ __forceinline__ void low_ry(const T* u, T* b, const T* fx, const T* fy, uint2 e)
+{
+    const int cc = e.x & 0xFFFF, pc = e.x >> 16, W = e.y & 0xFFFF;
+    T v = T(0.25) * (low_res(u, b, fx, fy, pc - W, W) + T(2) * low_res(u, b, fx, fy, pc, W) +
+                     low_res(u, b, fx, fy, pc + W, W));
+    b[cc] = (e.y >> 16) ? b[cc] + T(0.5) * v : v;
+}
+
+template <class T>
+__device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint2 e, T omega)
+{
+    const int c = e.x & 0xFFF, W = (e.x >> 12) & 0xFF;
+    const bool iodd = (e.x >> 20) & 1, jodd = (e.x >> 21) & 1;
+    const bool hx = (e.x >> 22) & 1, hy = (e.x >> 23) & 1;
+    const int rx = e.y & 0xFFFF, ry = e.y >> 16;
+    T vx = T(0), vy = T(0);
+    if (hx) vx = iodd ? T(0.5) * (u[rx] + u[rx + 1]) : u[rx];
+    if (hy) vy = jodd ? T(0.5) * (u[ry] + u[ry + W]) : u[ry];
+    T corr;
+    if (hx && hy) {
+        T cxv = fx[c - 1] + fx[c], cyv = fy[c - W] + fy[c];
+        T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+        corr = (x2 * s) * vx + (y2 * s) * vy;
     } else {
-        int plo, phi;
-        diag_range(D, w.pi, w.qi, plo, phi);
-        if (zero_init) {
-            for (int p = plo; p <= phi; ++p) {
-                WGrid<T> g = w.grid(p, D + 2 - p);
-                const int n = (g.nx + 1) * (g.ny + 1);
-                for (int k = w.lane; k < n; k += w.ls) g.u[k] = T(0);
-            }
-            SY::sync();
-        }
-        w_sweeps<T, SY>(w, D, plo, phi, nu1);
-        // restriction (Eq. (2.3)) in two passes: x-children are set, y-children are
-        // set or completed, so a two-parent child gets R_x/2 + R_y/2
-        for (int p = max(plo, 2); p <= phi; ++p) {
-            const int q = D + 2 - p;
-            WGrid<T> g = w.grid(p, q);
-            WGrid<T> c = w.grid(p - 1, q);
-            const T wgt = (q < w.qi) ? T(0.5) : T(1);
-            const int W = g.nx + 1, shc = p - 1, Wc = (1 << shc) + 1, n = (g.ny - 1) << shc;
-            for (int k = w.lane; k < n; k += w.ls) {
-                const int ic = k & ((1 << shc) - 1), j = 1 + (k >> shc);
-                if (ic == 0) continue;
-                const int cc = j * W + 2 * ic;
-                T v = T(0.25) * (w_res_at(g, cc - 1, W) + T(2) * w_res_at(g, cc, W) + w_res_at(g, cc + 1, W));
-                c.b[j * Wc + ic] = wgt * v;
-            }
-        }
-        SY::sync();
-        for (int p = plo; p <= phi; ++p) {
-            const int q = D + 2 - p;
-            if (q < 2) continue;
-            WGrid<T> g = w.grid(p, q);
-            WGrid<T> c = w.grid(p, q - 1);
-            const bool both = p < w.pi;  // child (p, q-1) also has the x-parent (p+1, q-1)
-            const int W = g.nx + 1, n = ((g.ny >> 1) - 1) << p;
-            for (int k = w.lane; k < n; k += w.ls) {
-                const int i = k & (g.nx - 1), jc = 1 + (k >> p);
-                if (i == 0) continue;
-                const int cc = 2 * jc * W + i;
-                T v = T(0.25) * (w_res_at(g, cc - W, W) + T(2) * w_res_at(g, cc, W) + w_res_at(g, cc + W, W));
-                if (both) c.b[jc * W + i] += T(0.5) * v;
-                else c.b[jc * W + i] = v;
-            }
-        }
-        SY::sync();
+        corr = hx ? vx : vy;
     }
+    u[c] += omega * corr;
 }
 
-template <class T, class SY, int D>
-__device__ __forceinline__ void w_post(const WarpLow<T>& w, int nu2, T omega)
+template <int NT>
+__device__ __forceinline__ void low_sync()
 {
-    int plo, phi;
-    diag_range(D, w.pi, w.qi, plo, phi);
-    for (int p = plo; p <= phi; ++p) {
-        const int q = D + 2 - p;
-        WGrid<T> g = w.grid(p, q);
-        const T* ucx = (p > 1) ? w.grid(p - 1, q).u : nullptr;
-        const T* ucy = (q > 1) ? w.grid(p, q - 1).u : nullptr;
-        const int W = g.nx + 1, n = (g.ny - 1) << p;
-        for (int k = w.lane; k < n; k += w.ls) {
-            const int i = k & (g.nx - 1), j = 1 + (k >> p);
-            if (i == 0) continue;
-            const int c = j * W + i;
-            T vx = T(0), vy = T(0);
-            if (ucx) {
-                const int Wc = (g.nx >> 1) + 1, r = j * Wc + (i >> 1);
-                vx = (i & 1) ? T(0.5) * (ucx[r] + ucx[r + 1]) : ucx[r];
-            }
-            if (ucy) {
-                const int r = (j >> 1) * W + i;
-                vy = (j & 1) ? T(0.5) * (ucy[r] + ucy[r + W]) : ucy[r];
-            }
-            T corr;
-            if (ucx && ucy) {
-                T cxv = g.ax[c - 1] + g.ax[c], cyv = g.ay[c - W] + g.ay[c];
-                T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
-                corr = (x2 * s) * vx + (y2 * s) * vy;
-            } else {
-                corr = ucx ? vx : vy;
-            }
-            g.u[c] += omega * corr;
-        }
-    }
-    SY::sync();
-    w_sweeps<T, SY>(w, D, plo, phi, nu2);
+    if constexpr (NT == 32) __syncwarp();
+    else __syncthreads();
 }
 
-// One mu-cycle of Algorithm 1 at diagonal D, unrolled at compile time.
-template <class T, class SY, int D>
-__device__ void w_cycle(const WarpLow<T>& w, int zero_init, const CycleParams& cp)
-{
-    w_pre<T, SY, D>(w, zero_init, cp.nu1);
-    if constexpr (D > 0) {
-        for (int k = 0; k < cp.mu; ++k) w_cycle<T, SY, D - 1>(w, k == 0, cp);
-        w_post<T, SY, D>(w, cp.nu2, (T)cp.omega);
-    }
-}
-
-template <class T, class SY>
-__device__ void w_mu_cycle(const WarpLow<T>& w, int d, int zero_init, const CycleParams& cp)
-{
-    static_assert(kDW == 4, "dispatch below covers diagonals 0..4");
-    switch (d) {
-    case 0: w_cycle<T, SY, 0>(w, zero_init, cp); break;
-    case 1: w_cycle<T, SY, 1>(w, zero_init, cp); break;
-    case 2: w_cycle<T, SY, 2>(w, zero_init, cp); break;
-    case 3: w_cycle<T, SY, 3>(w, zero_init, cp); break;
-    default: w_cycle<T, SY, 4>(w, zero_init, cp); break;
-    }
-}
-
-// `calls` mu-cycles at diagonal dl <= kDW of each item.  A warp carries
-// `group` items (1, 2 or 4), each on 32/group lanes, in lockstep: all items of
-// a launch run the same sequence of phases (same dl, mu, nu), so the warp
-// barriers line up and one instruction stream serves several items.
-// Reads the coefficients of the item's grids with d <= dl and the right-hand
-// side of its diagonal-dl grids (combined from the parents' restrictions, or
-// the item's own residual when dl is its top); writes back u of diagonal dl.
-template <class T, class SY>
-__global__ void __launch_bounds__(256) k_low_warp(DevCtx cx, int64_t nitems, int group, T* su,
-                                                            const T* sbx, const T* sby, const T* ax, const T* ay,
-                                                            int dl, int calls, int zero_init, CycleParams cp)
+// `calls` mu-cycles at diagonal dl <= kDW of each item, starting from zero.
+// NT = 32: blockDim.x / 32 items per CTA, one warp each; NT > 32: one item per
+// CTA of NT threads.  Reads the coefficients of the item's grids with
+// d <= dl and the right-hand side of its diagonal-dl grids (combined from the
+// parents' restrictions, or the item's own residual when dl is its top);
+// writes back u of diagonal dl.
+template <class T, int NT>
+__global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su, const T* sbx, const T* sby,
+                                             const T* ax, const T* ay, const LowDesc* descs, const uint2* ent,
+                                             const uint2* rprog, int dl, int calls, CycleParams cp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int toff[kDW + 2][kDW + 2];
-    if (threadIdx.x == 0) {
-        int o = 0;
-        for (int p = 1; p <= kDW + 1; ++p)
-            for (int q = 1; q <= kDW + 2 - p; ++q) {
-                toff[p][q] = o;
-                o += low_nodes(p, q);
-            }
-    }
-    __syncthreads();
-    // SyncWarp: `group` items per warp; SyncCta: one item per CTA on all its threads
-    const bool cta = std::is_same<SY, SyncCta>::value;
-    const int warp = cta ? 0 : (threadIdx.x >> 5), lane = cta ? threadIdx.x : (threadIdx.x & 31);
-    const int ls = cta ? (int)blockDim.x : 32 / group, sub = lane / ls, sl = lane % ls;
-    const int64_t first = cta ? (int64_t)blockIdx.x : ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * group;
-    if (first >= nitems) return;  // whole warp idle; no block-wide barrier below this point
-    const int64_t it = first + sub;
-    const bool valid = it < nitems;
-    WarpLow<T> w;
-    T* base = (T*)smem_raw + (size_t)(cta ? 0 : warp * group + sub) * 4 * kLowNodes;
-    w.u = base;
-    w.b = base + kLowNodes;
-    w.ax = base + 2 * kLowNodes;
-    w.ay = base + 3 * kLowNodes;
-    w.toff = toff;
-    w.lane = sl;
-    w.ls = ls;
-    TaskRef t{};
-    const SampleInfo* S = nullptr;
-    if (valid) {
-        t = resolve_at(cx, it);
-        S = &cx.samples[t.s];
-        w.pi = t.seg->pi;
-        w.qi = t.seg->qi;
-    } else {
-        w.pi = w.qi = 0;  // no grids: the slot follows the phases without work
-    }
-    for (int k = sl; k < kLowNodes; k += ls) w.u[k] = T(0);
-    for (int p = 1; p <= min(w.pi, dl + 1); ++p)
-        for (int q = 1; q <= min(w.qi, dl + 2 - p); ++q) {
-            const int n = low_nodes(p, q), o = toff[p][q];
-            const int64_t co = S->node_off + grid_offset(p, q, S->Q);
-            for (int k = sl; k < n; k += ls) {
-                w.ax[o + k] = ax[co + k];
-                w.ay[o + k] = ay[co + k];
-            }
-            if (p + q - 2 == dl) {
-                const int64_t so = t.scr + grid_offset(p, q, w.qi);
-                const bool hx = p < w.pi, hy = q < w.qi;
-                for (int k = sl; k < n; k += ls) {
-                    T v;
-                    if (hx && hy) v = T(0.5) * sbx[so + k] + T(0.5) * sby[so + k];
-                    else if (hy) v = sby[so + k];
-                    else v = sbx[so + k];  // x-parent only, or the item's own residual
-                    w.b[o + k] = v;
-                }
+    const int slot = threadIdx.x / NT, tid = threadIdx.x % NT;
+    const int64_t it = (int64_t)blockIdx.x * (blockDim.x / NT) + slot;
+    if (it >= nitems) return;  // a whole warp (NT = 32) or the whole CTA (NT > 32)
+    const TaskRef t = resolve_at(cx, it);
+    const SampleInfo& S = cx.samples[t.s];
+    const int pi = t.seg->pi, qi = t.seg->qi;
+    const LowDesc& C = descs[low_class(min(pi, dl + 1), min(qi, dl + 1), dl)];
+    const int nn = C.nn;
+    T* u = (T*)smem_raw + (size_t)slot * 4 * kLowNodes;
+    T* b = u + nn;
+    T* fx = b + nn;
+    T* fy = fx + nn;
+    for (int k = tid; k < nn; k += NT) u[k] = T(0);
+    for (int g = 0; g < C.ngrid; ++g) {
+        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, o = w >> 8, n = low_nodes(p, q);
+        const int64_t co = S.node_off + grid_offset(p, q, S.Q);
+        for (int k = tid; k < n; k += NT) {
+            fx[o + k] = ax[co + k];
+            fy[o + k] = ay[co + k];
+        }
+        if (p + q - 2 == dl) {
+            const int64_t so = t.scr + grid_offset(p, q, qi);
+            const bool hx = p < pi, hy = q < qi;
+            for (int k = tid; k < n; k += NT) {
+                T v;
+                if (hx && hy) v = T(0.5) * sbx[so + k] + T(0.5) * sby[so + k];
+                else if (hy) v = sby[so + k];
+                else v = sbx[so + k];  // x-parent only, or the item's own residual
+                b[o + k] = v;
             }
         }
-    SY::sync();
-    for (int c = 0; c < calls; ++c) w_mu_cycle<T, SY>(w, dl, c == 0 ? zero_init : 0, cp);
-    if (!valid) return;
-    int plo, phi;
-    diag_range(dl, w.pi, w.qi, plo, phi);
-    for (int p = plo; p <= phi; ++p) {
-        const int q = dl + 2 - p, n = low_nodes(p, q), o = toff[p][q];
-        T* dst = su + t.scr + grid_offset(p, q, w.qi);
-        for (int k = sl; k < n; k += ls) dst[k] = w.u[o + k];
+    }
+    low_sync<NT>();
+    const T omega = (T)cp.omega;
+    const uint2* rp = rprog + C.prog;
+    const int nops = C.nops;
+    for (int call = 0; call < calls; ++call) {
+        // software pipeline: the words of the next two phases and this lane's
+        // first entry of the next phase are in flight while a phase runs
+        uint2 op = nops > 0 ? rp[0] : make_uint2(0u, 0u);
+        uint2 op1 = nops > 1 ? rp[1] : make_uint2(0u, 0u);
+        uint2 e = low_first(ent, op, tid);
+        for (int o = 0; o < nops; ++o) {
+            const uint2 op2 = o + 2 < nops ? rp[o + 2] : make_uint2(0u, 0u);
+            const uint2 e1 = low_first(ent, op1, tid);
+            const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
+            if (tid < cnt) {
+                if (kind == LK_ZERO) {
+                    for (int k = tid; k < cnt; k += NT) u[off + k] = T(0);
+                } else if (kind <= LK_SMOOTH_BLACK) {
+                    low_smooth(u, b, fx, fy, e);
+                    for (int k = tid + NT; k < cnt; k += NT) low_smooth(u, b, fx, fy, ent[off + k]);
+                } else if (kind == LK_RX) {
+                    low_rx(u, b, fx, fy, e);
+                    for (int k = tid + NT; k < cnt; k += NT) low_rx(u, b, fx, fy, ent[off + k]);
+                } else if (kind == LK_RY) {
+                    low_ry(u, b, fx, fy, e);
+                    for (int k = tid + NT; k < cnt; k += NT) low_ry(u, b, fx, fy, ent[off + k]);
+                } else {
+                    low_prol(u, fx, fy, e, omega);
+                    for (int k = tid + NT; k < cnt; k += NT) low_prol(u, fx, fy, ent[off + k], omega);
+                }
+            }
+            low_sync<NT>();
+            op = op1;
+            op1 = op2;
+            e = e1;
+        }
+    }
+    for (int g = 0; g < C.ngrid; ++g) {
+        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, o = w >> 8;
+        if (p + q - 2 != dl) continue;
+        T* dst = su + t.scr + grid_offset(p, q, qi);
+        const int n = low_nodes(p, q);
+        for (int k = tid; k < n; k += NT) dst[k] = u[o + k];
     }
 }
 
@@ -1013,6 +944,156 @@ struct ItemType {
     int64_t stage_base;  // first flag index of this type in the stage's flag array
 };
 
+// ------------------------------------------------ low-diagonal host tables --
+
+// Tables of every class (independent of the solver parameters).
+struct LowTables {
+    std::vector<LowDesc> desc;  // [kLowClasses]
+    std::vector<uint2> ent;
+};
+
+static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<uint2>& ent)
+{
+    std::memset(&D, 0, sizeof(D));
+    D.dl = dl;
+    int toff[kDW + 3][kDW + 3];
+    int nn = 0;
+    auto exists = [&](int p, int q) { return p >= 1 && q >= 1 && p <= pic && q <= qic && p + q - 2 <= dl; };
+    for (int d = 0; d <= dl; ++d) {
+        D.off[d][LK_ZERO] = nn;
+        for (int p = 1; p <= d + 1; ++p) {
+            const int q = d + 2 - p;
+            if (!exists(p, q)) continue;
+            toff[p][q] = nn;
+            D.grid[D.ngrid++] = p | q << 4 | nn << 8;
+            nn += low_nodes(p, q);
+        }
+        D.cnt[d][LK_ZERO] = nn - D.off[d][LK_ZERO];
+    }
+    D.nn = nn;
+    for (int d = 0; d <= dl; ++d) {
+        for (int colour = 0; colour < 2; ++colour) {  // red: (i + j) even
+            D.off[d][LK_SMOOTH_RED + colour] = (int)ent.size();
+            for (int p = 1; p <= d + 1; ++p) {
+                const int q = d + 2 - p;
+                if (!exists(p, q)) continue;
+                const int nx = 1 << p, ny = 1 << q, W = nx + 1;
+                for (int j = 1; j < ny; ++j)
+                    for (int i = 1; i < nx; ++i)
+                        if (((i + j) & 1) == colour)
+                            ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * W + i) | (uint32_t)W << 16, 0u));
+            }
+            D.cnt[d][LK_SMOOTH_RED + colour] = (int)ent.size() - D.off[d][LK_SMOOTH_RED + colour];
+        }
+        if (d == 0) continue;
+        // Eq. (2.3): x-children (p-1, q) take R_x, halved when they also have the
+        // y-parent (p-1, q+1); y-children (p, q-1) add R_y/2 when they also have
+        // the x-parent (p+1, q-1), else take R_y
+        D.off[d][LK_RX] = (int)ent.size();
+        for (int p = 2; p <= d + 1; ++p) {
+            const int q = d + 2 - p;
+            if (!exists(p, q)) continue;
+            const int nx = 1 << p, ny = 1 << q, W = nx + 1, Wc = (nx >> 1) + 1;
+            const uint32_t half = q < qic ? 1u : 0u;
+            for (int j = 1; j < ny; ++j)
+                for (int ic = 1; ic < (nx >> 1); ++ic)
+                    ent.push_back(make_uint2((uint32_t)(toff[p - 1][q] + j * Wc + ic) |
+                                                 (uint32_t)(toff[p][q] + j * W + 2 * ic) << 16,
+                                             (uint32_t)W | half << 16));
+        }
+        D.cnt[d][LK_RX] = (int)ent.size() - D.off[d][LK_RX];
+        D.off[d][LK_RY] = (int)ent.size();
+        for (int p = 1; p <= d + 1; ++p) {
+            const int q = d + 2 - p;
+            if (q < 2 || !exists(p, q)) continue;
+            const int nx = 1 << p, ny = 1 << q, W = nx + 1;
+            const uint32_t both = p < pic ? 1u : 0u;
+            for (int jc = 1; jc < (ny >> 1); ++jc)
+                for (int i = 1; i < nx; ++i)
+                    ent.push_back(make_uint2((uint32_t)(toff[p][q - 1] + jc * W + i) |
+                                                 (uint32_t)(toff[p][q] + 2 * jc * W + i) << 16,
+                                             (uint32_t)W | both << 16));
+        }
+        D.cnt[d][LK_RY] = (int)ent.size() - D.off[d][LK_RY];
+        // Eq. (2.4)/(2.5): linear prolongation from each child, kappa-weighted
+        D.off[d][LK_PROL] = (int)ent.size();
+        for (int p = 1; p <= d + 1; ++p) {
+            const int q = d + 2 - p;
+            if (!exists(p, q)) continue;
+            const int nx = 1 << p, ny = 1 << q, W = nx + 1, Wc = (nx >> 1) + 1;
+            const bool hx = p > 1, hy = q > 1;
+            for (int j = 1; j < ny; ++j)
+                for (int i = 1; i < nx; ++i) {
+                    const uint32_t rx = hx ? (uint32_t)(toff[p - 1][q] + j * Wc + (i >> 1)) : 0u;
+                    const uint32_t ry = hy ? (uint32_t)(toff[p][q - 1] + (j >> 1) * W + i) : 0u;
+                    ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * W + i) | (uint32_t)W << 12 |
+                                                 (uint32_t)(i & 1) << 20 | (uint32_t)(j & 1) << 21 |
+                                                 (uint32_t)hx << 22 | (uint32_t)hy << 23,
+                                             rx | ry << 16));
+                }
+        }
+        D.cnt[d][LK_PROL] = (int)ent.size() - D.off[d][LK_PROL];
+    }
+}
+
+static const LowTables& low_tables()
+{
+    static const LowTables tabs = [] {
+        LowTables t;
+        t.desc.resize(kLowClasses);
+        for (int dl = 0; dl <= kDW; ++dl)
+            for (int pic = 1; pic <= dl + 1; ++pic)
+                for (int qic = 1; qic <= dl + 1; ++qic) low_build_class(pic, qic, dl, t.desc[low_class(pic, qic, dl)], t.ent);
+        return t;
+    }();
+    return tabs;
+}
+
+// Algorithm 1 below diagonal dl as a flat program (the recursion unrolled): the
+// visit of diagonal d zeroes it when it is the first of its parent's mu visits,
+// smooths nu1 times, restricts to diagonal d-1, recurses mu times, prolongs and
+// smooths nu2 times; diagonal 0 is solved exactly (one unknown).  The top is
+// not zeroed: the kernel starts every item from u = 0.
+static void low_program_rec(int d, bool zero, const msg_params& prm, std::vector<int>& prog)
+{
+    auto emit = [&](int kind, int dd) { prog.push_back(kind | dd << 3); };
+    if (d == 0) { emit(LK_SMOOTH_RED, 0); return; }
+    if (zero) emit(LK_ZERO, d);
+    for (int s = 0; s < prm.nu1; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
+    emit(LK_RX, d);
+    emit(LK_RY, d);
+    for (int k = 0; k < prm.mu; ++k) low_program_rec(d - 1, k == 0, prm, prog);
+    emit(LK_PROL, d);
+    for (int s = 0; s < prm.nu2; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
+}
+
+static std::vector<int> low_program(int dl, const msg_params& prm)
+{
+    std::vector<int> prog;
+    low_program_rec(dl, false, prm, prog);
+    return prog;
+}
+
+// Resolved programs of every class for these parameters: each (kind, diagonal)
+// word becomes {kind | entries << 3, first entry} of the class, phases with no
+// entries are dropped; desc[c].prog / nops locate class c's program.
+static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc)
+{
+    desc = low_tables().desc;
+    std::vector<int> words[kDW + 1];
+    for (int dl = 0; dl <= kDW; ++dl) words[dl] = low_program(dl, prm);
+    std::vector<uint2> rp;
+    for (LowDesc& D : desc) {
+        D.prog = (int)rp.size();
+        for (int w : words[D.dl]) {
+            const int kind = w & 7, d = w >> 3, cnt = D.cnt[d][kind];
+            if (cnt > 0) rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)D.off[d][kind]));
+        }
+        D.nops = (int)rp.size() - D.prog;
+    }
+    return rp;
+}
+
 struct Plan {
     int S = 0;
     std::vector<SampleInfo> samples;
@@ -1036,7 +1117,7 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
     if (S > 0 && !PQ) { set_error("PQ is NULL"); return MSG_ERR_INVALID; }
     if (!prm) { set_error("params is NULL"); return MSG_ERR_INVALID; }
     if (prm->mu < 1 || prm->mu > 3 || prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 ||
-        prm->max_cycles < 1 || !(prm->eps >= 0.0) || !(prm->omega > 0.0) || prm->omega > 2.0) {
+        prm->nu1 > 64 || prm->nu2 > 64 || prm->max_cycles < 1 || !(prm->eps >= 0.0) || !(prm->omega > 0.0) || prm->omega > 2.0) {
         set_error("invalid solver parameters");
         return MSG_ERR_INVALID;
     }
@@ -1049,13 +1130,9 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         set_error("tune_block must be 0 or a multiple of 32 in [32, 1024]");
         return MSG_ERR_INVALID;
     }
-    if (prm->tune_low_threads != 0 && (prm->tune_low_threads < 32 || prm->tune_low_threads > 256 ||
-                                       prm->tune_low_threads % 32)) {
-        set_error("tune_low_threads must be 0 or a multiple of 32 in [32, 256]");
-        return MSG_ERR_INVALID;
-    }
-    if (prm->tune_low_group != 0 && prm->tune_low_group != 1 && prm->tune_low_group != 2 && prm->tune_low_group != 4) {
-        set_error("tune_low_group must be 0, 1, 2 or 4");
+    if (prm->tune_low_threads != 0 && prm->tune_low_threads != 32 && prm->tune_low_threads != 64 &&
+        prm->tune_low_threads != 128) {
+        set_error("tune_low_threads must be 0, 32, 64 or 128");
         return MSG_ERR_INVALID;
     }
     if (prm->tune_stage_from < 0 || prm->tune_warp_visit < 0 || prm->tune_warp_visit > 24) {
@@ -1166,13 +1243,15 @@ struct WsLayout {
     size_t samples, perm, gpos, groups, allsegs;
     size_t nstep, cycles_i, relres_i;
     size_t u64, ax64, ay64, ax32, ay32;
+    size_t low_desc, low_ent, low_prog;  // tables of the low-diagonal program
     // per stage L: segment list, sample list, flags, counter, scratch (su, sbx, sby)
     std::vector<size_t> segs, slist, sflag, counter, su, sbx, sby;
     size_t total;
 };
 
-WsLayout layout_of(const Plan& pl, int precision)
+WsLayout layout_of(const Plan& pl, const msg_params& prm)
 {
+    const int precision = prm.precision;
     WsLayout w{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
@@ -1181,6 +1260,12 @@ WsLayout layout_of(const Plan& pl, int precision)
     w.gpos = take(sizeof(int) * pl.S);
     w.groups = take(sizeof(Group) * pl.groups.size() * (pl.Lmax + 2));
     w.allsegs = take(sizeof(Segment) * pl.all_segs.size());
+    {
+        std::vector<LowDesc> desc;
+        w.low_desc = take(sizeof(LowDesc) * kLowClasses);
+        w.low_ent = take(sizeof(uint2) * low_tables().ent.size());
+        w.low_prog = take(sizeof(uint2) * low_resolve(prm, desc).size());
+    }
     w.nstep = take(sizeof(int) * pl.total_q);
     w.cycles_i = take(sizeof(int) * pl.total_q);
     w.relres_i = take(sizeof(double) * pl.total_q);
@@ -1257,11 +1342,13 @@ struct SolveCtx {
     double* rel;
     CycleParams cp;
     int block;      // threads per CTA of the PRE/POST visit kernels
-    int low_warps;  // items (warps) per CTA of the warp-resident kernel
+    int low_warps;  // items (warps) per CTA of the low-diagonal kernel with one warp per item
     int warp_visit_max;  // diagonals up to this one are visited with one warp per task
     int stage_from;      // diagonals from this one on are staged in shared memory when they fit
-    int low_group;       // items per warp in the warp-resident kernel
-    int low_threads;     // > 32: one item per CTA of this many threads
+    int low_threads;     // threads per item of the low-diagonal kernel: 32, 64 or 128
+    const LowDesc* low_desc;
+    const uint2* low_ent;
+    const uint2* low_prog;  // resolved programs of all classes
 };
 
 // Stage L of FMSG for the samples handed over by stage L-1: cubic
@@ -1492,19 +1579,19 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         if (rc != MSG_OK) return finish(rc);
         DevCtx ic = ctx_of(0, item_nseg);
         bool launch_err = false;
-        auto launch_low = [&](int d, int calls, int zi) {
+        auto launch_low = [&](int d, int calls) {
             prof_begin(K_LOW, st);
-            if (C.low_threads > 32) {  // one item per CTA
-                const size_t shm = sizeof(T) * 4 * kLowNodes;
-                k_low_warp<T, SyncCta><<<(unsigned)nitems, C.low_threads, shm, st>>>(ic, nitems, 1, su, sbx, sby, C.ax,
-                                                                                   C.ay, d, calls, zi, C.cp);
+            if (C.low_threads == 32) {  // one warp per item, low_warps items per CTA
+                const int lw = C.low_warps;
+                const unsigned nb = (unsigned)((nitems + lw - 1) / lw);
+                k_low<T, 32><<<nb, lw * 32, sizeof(T) * 4 * kLowNodes * lw, st>>>(
+                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
+            } else if (C.low_threads == 64) {  // one item per CTA
+                k_low<T, 64><<<(unsigned)nitems, 64, sizeof(T) * 4 * kLowNodes, st>>>(
+                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             } else {
-                const int lw = C.low_warps, gi = C.low_group;
-                const size_t shm = sizeof(T) * 4 * kLowNodes * lw * gi;
-                const int64_t per_cta = (int64_t)lw * gi;
-                const unsigned nb = (unsigned)((nitems + per_cta - 1) / per_cta);
-                k_low_warp<T, SyncWarp><<<nb, lw * 32, shm, st>>>(ic, nitems, gi, su, sbx, sby, C.ax, C.ay, d, calls,
-                                                                  zi, C.cp);
+                k_low<T, 128><<<(unsigned)nitems, 128, sizeof(T) * 4 * kLowNodes, st>>>(
+                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             }
             prof_end(K_LOW, st, low_bytes, 0.0);
             launch_err |= cudaGetLastError() != cudaSuccess;
@@ -1540,7 +1627,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
         if (L <= kLowCut) {
-            launch_low(L, 1, 1);
+            launch_low(L, 1);
         } else {
             struct Frame { int d, k, zi, phase; };
             std::vector<Frame> stack;
@@ -1551,7 +1638,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
                     launch_half(f.d, 1, f.zi);
                     f.phase = 1;
                     if (f.d - 1 <= kLowCut) {
-                        launch_low(f.d - 1, C.prm.mu, 1);
+                        launch_low(f.d - 1, C.prm.mu);
                         f.phase = 2;
                     }
                     continue;
@@ -1597,9 +1684,9 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
                   (const double*)(ws + wl.ax64), (const double*)(ws + wl.ay64), nullptr, nullptr,
                   (int*)(ws + wl.nstep), (int*)(ws + wl.cycles_i), (double*)(ws + wl.relres_i),
                   CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kThreads,
-                  prm.tune_low_warps ? prm.tune_low_warps : 4, prm.tune_warp_visit ? prm.tune_warp_visit : kDW,
-                  prm.tune_stage_from ? prm.tune_stage_from : 99, prm.tune_low_group ? prm.tune_low_group : 2,
-                  prm.tune_low_threads ? prm.tune_low_threads : 32};
+                  prm.tune_low_warps ? prm.tune_low_warps : 2, prm.tune_warp_visit ? prm.tune_warp_visit : kDW,
+                  prm.tune_stage_from ? prm.tune_stage_from : 99, prm.tune_low_threads ? prm.tune_low_threads : 32,
+                  (const LowDesc*)(ws + wl.low_desc), (const uint2*)(ws + wl.low_ent), (const uint2*)(ws + wl.low_prog)};
     float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
     float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
     C.ax = mixed ? (const T*)ax32 : (const T*)(ws + wl.ax64);
@@ -1625,13 +1712,29 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-    if (sizeof(T) * 4 * kLowNodes * C.low_warps * C.low_group > kStageSmemMax + 24 * 1024) {
-        set_error("tune_low_warps * tune_low_group items do not fit the shared memory of one CTA");
+    if (sizeof(T) * 4 * kLowNodes * C.low_warps > kStageSmemMax + 24 * 1024) {
+        set_error("tune_low_warps items do not fit the shared memory of one CTA");
         return MSG_ERR_INVALID;
     }
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T, SyncWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes * C.low_warps * C.low_group)));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low_warp<T, SyncCta>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    {
+        // tables of the low-diagonal program: class descriptors, node entries, programs
+        const LowTables& lt = low_tables();
+        std::vector<LowDesc> desc;
+        const std::vector<uint2> rp = low_resolve(prm, desc);
+        MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_desc, desc.data(), sizeof(LowDesc) * desc.size(),
+                                     cudaMemcpyHostToDevice, st));
+        MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_ent, lt.ent.data(), sizeof(uint2) * lt.ent.size(),
+                                     cudaMemcpyHostToDevice, st));
+        MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_prog, rp.data(), sizeof(uint2) * rp.size(),
+                                     cudaMemcpyHostToDevice, st));
+        // the sources are host vectors: finish the copies before they go out of scope
+        MSG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * 4 * kLowNodes * C.low_warps)));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * 4 * kLowNodes)));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * 4 * kLowNodes)));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_post_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
@@ -1693,7 +1796,7 @@ extern "C" size_t msg_workspace_bytes(const int32_t* PQ, int64_t S, const msg_pa
     Plan pl;
     build_plan(PQ, S, pl);
     // the per-sample status array is kept inside the workspace when the caller passes none
-    return layout_of(pl, prm->precision).total + align_up(sizeof(int32_t) * std::max<int64_t>(S, 1));
+    return layout_of(pl, *prm).total + align_up(sizeof(int32_t) * std::max<int64_t>(S, 1));
 }
 
 extern "C" int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, const double* Z, double* Qout,
@@ -1707,7 +1810,7 @@ extern "C" int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_param
     if (!Z || !Qout || !workspace) { set_error("Z, Qout and workspace must be non-NULL"); return MSG_ERR_INVALID; }
     Plan pl;
     build_plan(PQ, S, pl);
-    WsLayout wl = layout_of(pl, prm->precision);
+    WsLayout wl = layout_of(pl, *prm);
     const size_t need = wl.total + align_up(sizeof(int32_t) * S);
     if (ws_bytes < need) {
         set_error("workspace too small: need " + std::to_string(need) + " bytes");

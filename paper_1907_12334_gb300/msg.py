@@ -40,7 +40,7 @@ class msg_params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32),
                 ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32),
                 ("tune_warp_visit", ctypes.c_int32), ("tune_stage_from", ctypes.c_int32),
-                ("tune_low_group", ctypes.c_int32), ("tune_low_threads", ctypes.c_int32)]
+                ("tune_low_threads", ctypes.c_int32)]
 
 
 @dataclass
@@ -59,13 +59,12 @@ class SolverParams:
     tune_low_warps: int = 0
     tune_warp_visit: int = 0
     tune_stage_from: int = 0
-    tune_low_group: int = 0
     tune_low_threads: int = 0
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
                           self.qoi, self.coef, self.tune_block, self.tune_low_warps, self.tune_warp_visit,
-                          self.tune_stage_from, self.tune_low_group, self.tune_low_threads)
+                          self.tune_stage_from, self.tune_low_threads)
 
 
 _lib = None
