@@ -28,6 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSG samples/s at QoI rel err <=1e-8 vs plain FP64"
+# every launch is counted; a random 1/PROFILE_STRIDE of each kernel class's launches is timed
+# with CUDA events inside the timed region (timing every one costs ~10% of the step on the host)
+PROFILE_STRIDE = 16
 
 
 def parse():
@@ -50,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=0, help="oracle samples for the CPU baseline (0: one per core)")
+    ap.add_argument("--profile-levels", default="", metavar="PATH",
+                    help="after the timed region, run one more step timing every launch and write the "
+                         "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
     return ap.parse_args()
 
 
@@ -218,8 +224,7 @@ def ours(a, rank, world, local_rank):
         msg.msg_normals(seed, 0, S, M, xi)
         msg.sample_field(prep, npts, M, gemm, xi, Z)
         prm = autotune.tune(PQ, Z.reshape(-1), prm, sample=min(S, 512))
-        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps,
-                 "tune_warp_visit": prm.tune_warp_visit}
+        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps}
 
     def step(k):
         s0 = (k * world + rank) * S
@@ -239,7 +244,7 @@ def ours(a, rank, world, local_rank):
         tdist.barrier()
 
     # ---- timed region (device time, CUDA events on the launching stream)
-    msg.msg_profile_enable(True)
+    msg.msg_profile_enable(True, stride=PROFILE_STRIDE)
     launches0 = msg.msg_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     conv = []
@@ -287,6 +292,23 @@ def ours(a, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e_conv = float((h_st.numpy() == 0).mean())
     e2e_val = None if a.no_e2e else world * S * a.steps * e2e_conv / e2e_s
+
+    # ---- optional: one untimed step with every launch timed, per multigrid diagonal
+    if a.profile_levels and rank == 0:
+        msg.msg_profile_enable(True, stride=1)
+        step(a.warmup + 2 * a.steps)
+        torch.cuda.synchronize(dev)
+        levels = {}
+        for c in ("PRE", "POST", "LOW"):
+            for d in range(P + Q - 1):
+                r = msg.msg_profile_read_level(c, d)
+                if r["timed"]:
+                    levels.setdefault(c, {})[d] = {"launches": r["timed"], "ms": round(r["ms"], 3),
+                                                   "avg_us": round(1000 * r["ms"] / r["timed"], 2),
+                                                   "bytes_per_launch": r["bytes"] / r["timed"]}
+        msg.msg_profile_enable(False)
+        with open(a.profile_levels, "w") as f:
+            json.dump({"workload": workload_name(a), "levels": levels}, f, indent=1)
 
     # ---- roofline of the dominant kernel (largest event-timed share)
     hbm, bf16, peak_src = measured_peaks()

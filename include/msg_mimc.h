@@ -76,10 +76,8 @@ typedef struct {
     int32_t precision;  /* MSG_PREC_* */
     int32_t qoi;        /* MSG_QOI_* */
     int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
-    int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 256; multiple of 32) */
+    int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 128; multiple of 32) */
     int32_t tune_low_warps; /* launch shape: items per CTA of the low-diagonal kernel at one warp per item (0: 2; 1..8) */
-    int32_t tune_warp_visit; /* launch shape: diagonals <= this are visited one warp per grid (0: none beyond the warp-resident ones); 0..24 */
-    int32_t tune_stage_from; /* launch shape: diagonals >= this stage their grid in shared memory when it fits (0: none) */
     int32_t tune_low_threads; /* launch shape: threads per item there: 32, or 64/128 for one item per CTA (0: 32) */
 } msg_params;
 
@@ -178,17 +176,24 @@ int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t p0, int32_
 /* Instrumentation (no counterpart in the paper).                           */
 /*                                                                          */
 /* msg_launch_count: number of CUDA kernels this library has launched in this */
-/* process.  msg_profile_enable(1) clears the records and starts timing every  */
-/* launch with CUDA events on its own stream (0 stops); msg_profile_read sums, */
-/* for one kernel class, the launches, their event-timed milliseconds and      */
-/* their algorithmic bytes and flops (the compulsory traffic/work per launch   */
-/* as defined in the design notes).  Classes: 0 PRE, 1 POST, 2 LOW (cycle      */
-/* visits above / at-and-below the cut), 3 RESIDUAL, 4 UPDATE, 5 INTERP,        */
-/* 6 QOI, 7 COEFFS, 8 NORMALS, 9 KL, 10 MIMC.  msg_profile_read synchronises    */
-/* the recorded events.                                                      */
+/* process.  msg_profile_enable(n), n >= 1, clears the records, counts every  */
+/* launch of each kernel class and times a random 1/n of them with CUDA       */
+/* events on their own streams (0 stops; n > 1 keeps the event overhead off   */
+/* most launches).  msg_profile_read returns, for one kernel class, the       */
+/* launches counted and the event-timed milliseconds, algorithmic bytes and   */
+/* flops (the compulsory traffic/work per launch as defined in the design     */
+/* notes) of the timed ones, scaled by launches / timed launches (exact for   */
+/* n = 1).  Classes: 0 PRE, 1 POST, 2 LOW (cycle visits above / at-and-below  */
+/* the cut), 3 RESIDUAL, 4 UPDATE, 5 INTERP, 6 QOI, 7 COEFFS, 8 NORMALS, 9 KL,*/
+/* 10 MIMC.  msg_profile_read synchronises the recorded events.               */
 int64_t msg_launch_count(void);
 int32_t msg_profile_enable(int32_t on);
 int32_t msg_profile_read(int32_t kernel_class, int64_t* launches, double* total_ms, double* bytes, double* flops);
+/* msg_profile_read_level: the unscaled sums over the timed launches of one   */
+/* class at one multigrid diagonal `level` (PRE/POST: the visited diagonal;  */
+/* LOW: the diagonal the low program starts from); profile with n = 1 to     */
+/* time every launch.                                                        */
+int32_t msg_profile_read_level(int32_t kernel_class, int32_t level, int64_t* timed, double* total_ms, double* bytes);
 
 /* Description of the last error on this thread ("" if none). */
 const char* msg_last_error(void);

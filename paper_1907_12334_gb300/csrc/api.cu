@@ -1,5 +1,6 @@
 // api.cu -- error state, version, launch counting and profiling of the C ABI.
 #include <atomic>
+#include <cstdint>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -14,12 +15,14 @@ std::atomic<int64_t> g_launches{0};
 
 struct Rec {
     cudaEvent_t a, b;
-    int cls;
+    int cls, level;
     double bytes, flops;
 };
 struct Prof {
     std::mutex mu;
-    bool on = false;
+    std::atomic<int> stride{0};              // 0: off; n: time a random 1/n of each class's launches
+    std::atomic<int64_t> count[K_NCLASS];    // launches of each class since enable
+    Prof() { for (auto& c : count) c = 0; }
     std::vector<cudaEvent_t> pool;
     size_t next = 0;
     std::vector<Rec> recs;
@@ -34,6 +37,19 @@ struct Prof {
     }
 } g_prof;
 thread_local cudaEvent_t t_pending_start[K_NCLASS];  // begin events of this thread's open launches
+thread_local bool t_pending_timed[K_NCLASS];
+thread_local uint64_t t_rng = 0;  // xorshift64 state of this thread's sampling decisions
+
+// true with probability 1/n (n >= 1)
+bool sample_one_in(int n)
+{
+    if (n <= 1) return true;
+    if (t_rng == 0) t_rng = 0x9E3779B97F4A7C15ull ^ (uint64_t)(uintptr_t)&t_rng;
+    t_rng ^= t_rng << 13;
+    t_rng ^= t_rng >> 7;
+    t_rng ^= t_rng << 17;
+    return t_rng % (uint64_t)n == 0;
+}
 }  // namespace
 
 void set_error(const std::string& what) { g_last_error = what; }
@@ -41,21 +57,27 @@ void clear_error() { g_last_error.clear(); }
 
 void prof_begin(int cls, cudaStream_t st)
 {
-    if (!g_prof.on) return;
+    t_pending_timed[cls] = false;
+    const int n = g_prof.stride.load(std::memory_order_relaxed);
+    if (n <= 0) return;
+    g_prof.count[cls].fetch_add(1, std::memory_order_relaxed);
+    if (!sample_one_in(n)) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.take();
     cudaEventRecord(e, st);
     t_pending_start[cls] = e;
+    t_pending_timed[cls] = true;
 }
 
-void prof_end(int cls, cudaStream_t st, double bytes, double flops)
+void prof_end(int cls, cudaStream_t st, double bytes, double flops, int level)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof.on) return;
+    if (!t_pending_timed[cls]) return;
+    t_pending_timed[cls] = false;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.take();
     cudaEventRecord(e, st);
-    g_prof.recs.push_back(Rec{t_pending_start[cls], e, cls, bytes, flops});
+    g_prof.recs.push_back(Rec{t_pending_start[cls], e, cls, level, bytes, flops});
 }
 
 void prof_count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -71,10 +93,40 @@ extern "C" int64_t msg_launch_count(void) { return g_launches.load(); }
 extern "C" int32_t msg_profile_enable(int32_t on)
 {
     clear_error();
+    if (on < 0) {
+        set_error("msg_profile_enable: on must be >= 0");
+        return MSG_ERR_INVALID;
+    }
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    g_prof.on = on != 0;
+    g_prof.stride = 0;
     g_prof.recs.clear();
     g_prof.next = 0;
+    for (auto& c : g_prof.count) c = 0;
+    g_prof.stride = on;
+    return MSG_OK;
+}
+
+// Sums over the timed launches of one class (and level, if level >= 0).
+static int32_t profile_sum(int32_t cls, int32_t level, int64_t* timed, double* ms_out, double* by_out, double* fl_out)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    int64_t n = 0;
+    double ms = 0.0, by = 0.0, fl = 0.0;
+    for (const Rec& r : g_prof.recs) {
+        if (r.cls != cls || (level >= 0 && r.level != level)) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MSG_ERR_CUDA; }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        ms += t;
+        by += r.bytes;
+        fl += r.flops;
+        ++n;
+    }
+    *timed = n;
+    *ms_out = ms;
+    *by_out = by;
+    *fl_out = fl;
     return MSG_OK;
 }
 
@@ -85,23 +137,27 @@ extern "C" int32_t msg_profile_read(int32_t cls, int64_t* launches, double* tota
         set_error("msg_profile_read: bad arguments");
         return MSG_ERR_INVALID;
     }
-    std::lock_guard<std::mutex> lk(g_prof.mu);
     int64_t n = 0;
     double ms = 0.0, by = 0.0, fl = 0.0;
-    for (const Rec& r : g_prof.recs) {
-        if (r.cls != cls) continue;
-        cudaError_t e = cudaEventSynchronize(r.b);
-        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MSG_ERR_CUDA; }
-        float t = 0.f;
-        cudaEventElapsedTime(&t, r.a, r.b);
-        ms += t;
-        by += r.bytes;
-        fl += r.flops;
-        ++n;
-    }
-    *launches = n;
-    *total_ms = ms;
-    *bytes = by;
-    *flops = fl;
+    const int32_t rc = profile_sum(cls, -1, &n, &ms, &by, &fl);
+    if (rc != MSG_OK) return rc;
+    // every launch is counted, a random 1/stride of them is timed: scale the timed sums
+    const int64_t all = g_prof.count[cls].load();
+    const double scale = n > 0 ? (double)all / (double)n : 0.0;
+    *launches = all;
+    *total_ms = ms * scale;
+    *bytes = by * scale;
+    *flops = fl * scale;
     return MSG_OK;
+}
+
+extern "C" int32_t msg_profile_read_level(int32_t cls, int32_t level, int64_t* timed, double* total_ms, double* bytes)
+{
+    clear_error();
+    if (cls < 0 || cls >= K_NCLASS || level < 0 || !timed || !total_ms || !bytes) {
+        set_error("msg_profile_read_level: bad arguments");
+        return MSG_ERR_INVALID;
+    }
+    double fl = 0.0;
+    return profile_sum(cls, level, timed, total_ms, bytes, &fl);
 }

@@ -21,10 +21,12 @@ enum KernelClass {
 };
 
 // Every kernel launch of the library goes through these two calls:
-//   prof_begin(cls, st) before the launch, prof_end(cls, st, bytes, flops) after.
-// They count launches always and record CUDA events on `st` while profiling is on.
+//   prof_begin(cls, st) before the launch, prof_end(cls, st, bytes, flops, level) after.
+// They count launches always and, while profiling is on, record CUDA events on
+// `st` for a random 1/n of each class's launches.  `level` tags multigrid
+// launches with their diagonal (-1: none).
 void prof_begin(int cls, cudaStream_t st);
-void prof_end(int cls, cudaStream_t st, double bytes, double flops);
+void prof_end(int cls, cudaStream_t st, double bytes, double flops, int level = -1);
 // count one launch without recording events
 void prof_count();
 

@@ -15,7 +15,8 @@
 // d > kDW of the items' hierarchies are visited by one launch per visit half
 // (PRE: zero/smooth nu1/restrict; POST: prolong/smooth nu2) with one CTA per
 // (item, grid) task; everything at or below kDW runs inside one launch (LOW)
-// with one warp per item walking the recursion of Algorithm 1 in shared memory.
+// with one warp per item executing the recursion of Algorithm 1 as a flat
+// program in shared memory.
 //
 // Storage (all node-indexed with the boundary, see common.cuh):
 //   u64          solution of every grid of every sample (FP64)
@@ -171,18 +172,12 @@ __device__ __forceinline__ T res_at(const GView<T>& g, int c, int W)
     return b_at(g, c) - Au;
 }
 
-// Thread groups that run one grid operation: a whole CTA (large grids) or one
-// warp (small grids, several tasks per CTA).  `tid` and `n` index the group's
-// threads; sync() orders the group's shared and global memory accesses.
+// The thread group that runs one grid operation: a whole CTA.  `tid` and `n`
+// index its threads; sync() orders its shared and global memory accesses.
 struct CtaGroup {
     int tid, n;
     __device__ CtaGroup() : tid(threadIdx.x), n(blockDim.x) {}
     __device__ void sync() const { __syncthreads(); }
-};
-struct WarpGroup {
-    int tid, n;
-    __device__ WarpGroup() : tid(threadIdx.x & 31), n(32) {}
-    __device__ void sync() const { __syncwarp(); }
 };
 
 // CTA-wide: zero u on every node, boundary included.  Scratch is reused by
@@ -388,106 +383,6 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
     if (!resolve_2d(cx, t)) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
     visit_post(CtaGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
-}
-
-// The visit halves with the task's grid staged in shared memory: u, the
-// combined right-hand side and both coefficient arrays are read from global
-// memory once, all sweeps, the residuals of the restriction and the
-// prolongation work on the staged copy, and u is written back once.  Used for
-// grids whose four node arrays fit the launch's dynamic shared memory.
-template <class T>
-__device__ GView<T> stage_grid(const GView<T>& g, bool load_u, T* sm)
-{
-    const int n = (g.nx + 1) * (g.ny + 1);
-    T* su = sm;
-    T* sb = sm + n;
-    T* sax = sm + 2 * n;
-    T* say = sm + 3 * n;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        su[k] = load_u ? g.u[k] : T(0);
-        sb[k] = b_at(g, k);
-        sax[k] = g.ax[k];
-        say[k] = g.ay[k];
-    }
-    __syncthreads();
-    GView<T> s = g;
-    s.u = su;
-    s.bx = sb;
-    s.by = sb;
-    s.bmode = 0;
-    s.ax = sax;
-    s.ay = say;
-    return s;
-}
-
-template <class T>
-__device__ void unstage_u(const GView<T>& g, const T* su)
-{
-    const int n = (g.nx + 1) * (g.ny + 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) g.u[k] = su[k];
-}
-
-template <class T>
-__global__ void k_pre_s(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TaskRef t;
-    if (!resolve_2d(cx, t)) return;
-    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    const int p = t.seg->p, q = t.seg->q;
-    const CtaGroup grp;
-    GView<T> g = view_of(h, p, q);
-    if (p == 1 && q == 1) { cta_coarsest(grp, g); return; }
-    GView<T> s = stage_grid(g, !zero_init, (T*)smem_raw);  // zero_init: u starts at 0 (boundary included)
-    cta_smooth(grp, s, nu1);
-    T* cxb = (p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
-    T* cyb = (q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    cta_restrict(grp, s, cxb, cyb);
-    unstage_u(g, s.u);
-}
-
-template <class T>
-__global__ void k_post_s(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2, double omega)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TaskRef t;
-    if (!resolve_2d(cx, t)) return;
-    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    const int p = t.seg->p, q = t.seg->q;
-    if (p == 1 && q == 1) return;
-    const CtaGroup grp;
-    GView<T> g = view_of(h, p, q);
-    GView<T> s = stage_grid(g, true, (T*)smem_raw);
-    const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
-    const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    cta_prolong(grp, s, ucx, ucy, (T)omega);
-    cta_smooth(grp, s, nu2);
-    unstage_u(g, s.u);
-}
-
-// The same visit halves with one warp per (item, grid) task, for grids small
-// enough that a CTA per task would leave most of its threads idle and pay CTA
-// barriers for a few hundred points.
-template <class T>
-__global__ void k_pre_w(DevCtx cx, int64_t ntasks, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init,
-                        int nu1)
-{
-    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (task >= ntasks) return;  // whole warps; no block barrier below
-    TaskRef t = resolve_at(cx, task);
-    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    visit_pre(WarpGroup(), h, t.seg->p, t.seg->q, zero_init, nu1);
-}
-
-template <class T>
-__global__ void k_post_w(DevCtx cx, int64_t ntasks, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2,
-                         double omega)
-{
-    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (task >= ntasks) return;
-    TaskRef t = resolve_at(cx, task);
-    Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    visit_post(WarpGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
 // ---------------------------------------------- table-driven low diagonals --
@@ -1135,10 +1030,6 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         set_error("tune_low_threads must be 0, 32, 64 or 128");
         return MSG_ERR_INVALID;
     }
-    if (prm->tune_stage_from < 0 || prm->tune_warp_visit < 0 || prm->tune_warp_visit > 24) {
-        set_error("tune_warp_visit must be in [0, 24]");
-        return MSG_ERR_INVALID;
-    }
     if (prm->tune_low_warps < 0 || prm->tune_low_warps > kLowWarpsMax) {
         set_error("tune_low_warps must be in [0, 8]");
         return MSG_ERR_INVALID;
@@ -1294,7 +1185,8 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
 }
 
 constexpr int kThreads = 256;
-constexpr size_t kStageSmemMax = 200 * 1024;  // grids staged in shared memory up to this many bytes
+constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory of one CTA
+constexpr int kVisitThreads = 128;       // threads per CTA of the PRE/POST visit kernels (default)
 constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-resident, one launch
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
@@ -1343,8 +1235,6 @@ struct SolveCtx {
     CycleParams cp;
     int block;      // threads per CTA of the PRE/POST visit kernels
     int low_warps;  // items (warps) per CTA of the low-diagonal kernel with one warp per item
-    int warp_visit_max;  // diagonals up to this one are visited with one warp per task
-    int stage_from;      // diagonals from this one on are staged in shared memory when they fit
     int low_threads;     // threads per item of the low-diagonal kernel: 32, 64 or 128
     const LowDesc* low_desc;
     const uint2* low_ent;
@@ -1593,37 +1483,22 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
                 k_low<T, 128><<<(unsigned)nitems, 128, sizeof(T) * 4 * kLowNodes, st>>>(
                     ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             }
-            prof_end(K_LOW, st, low_bytes, 0.0);
+            prof_end(K_LOW, st, low_bytes, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
         auto launch_half = [&](int d, int pre, int zi) {
             if (dnseg[d] == 0) return;
-            const Segment& last = h_segs[dseg0[d] + dnseg[d] - 1];
-            const int64_t nb = last.blk_start + last.count;
             DevCtx c = ctx_of(dseg0[d], dnseg[d]);
-            // largest grid of this diagonal among the launch's tasks: staged in shared memory if it fits
-            int64_t maxn = 0;
-            for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k)
-                maxn = std::max<int64_t>(maxn, (int64_t)((1 << h_segs[k].p) + 1) * ((1 << h_segs[k].q) + 1));
-            const size_t shm = sizeof(T) * 4 * (size_t)maxn;
             prof_begin(pre ? K_PRE : K_POST, st);
             int64_t maxc = 0;
             for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k) maxc = std::max<int64_t>(maxc, h_segs[k].count);
             const dim3 g2((unsigned)maxc, (unsigned)dnseg[d]);  // x: sample in segment, y: segment
-            if (d >= C.stage_from && shm <= kStageSmemMax) {  // CTA per task, grid staged in shared memory
-                if (pre) k_pre_s<T><<<g2, C.block, shm, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
-                else k_post_s<T><<<g2, C.block, shm, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
-            } else if (d <= C.warp_visit_max) {  // one warp per task
-                const int wpb = 8;
-                const unsigned g = (unsigned)((nb + wpb - 1) / wpb);
-                if (pre) k_pre_w<T><<<g, wpb * 32, 0, st>>>(c, nb, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
-                else k_post_w<T><<<g, wpb * 32, 0, st>>>(c, nb, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
-            } else if (pre) {
+            if (pre) {
                 k_pre<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
             } else {
                 k_post<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
             }
-            prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0);
+            prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
         if (L <= kLowCut) {
@@ -1683,9 +1558,8 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     SolveCtx<T> C{pl, wl, ws, prm, Z, stat, DevCtx{}, (const Group*)(ws + wl.groups), (double*)(ws + wl.u64),
                   (const double*)(ws + wl.ax64), (const double*)(ws + wl.ay64), nullptr, nullptr,
                   (int*)(ws + wl.nstep), (int*)(ws + wl.cycles_i), (double*)(ws + wl.relres_i),
-                  CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kThreads,
-                  prm.tune_low_warps ? prm.tune_low_warps : 2, prm.tune_warp_visit ? prm.tune_warp_visit : kDW,
-                  prm.tune_stage_from ? prm.tune_stage_from : 99, prm.tune_low_threads ? prm.tune_low_threads : 32,
+                  CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kVisitThreads,
+                  prm.tune_low_warps ? prm.tune_low_warps : 2, prm.tune_low_threads ? prm.tune_low_threads : 32,
                   (const LowDesc*)(ws + wl.low_desc), (const uint2*)(ws + wl.low_ent), (const uint2*)(ws + wl.low_prog)};
     float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
     float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
@@ -1712,7 +1586,7 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-    if (sizeof(T) * 4 * kLowNodes * C.low_warps > kStageSmemMax + 24 * 1024) {
+    if (sizeof(T) * 4 * kLowNodes * C.low_warps > kSmemMax) {
         set_error("tune_low_warps items do not fit the shared memory of one CTA");
         return MSG_ERR_INVALID;
     }
@@ -1736,8 +1610,6 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
                                       (int)(sizeof(T) * 4 * kLowNodes)));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * 4 * kLowNodes)));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_post_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemMax));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- one worker (host thread + stream) per stage

@@ -26,7 +26,7 @@ MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
             "msg_solve_batch", "mimc_differences", "msg_last_error", "msg_version", "msg_launch_count",
-            "msg_profile_enable", "msg_profile_read")
+            "msg_profile_enable", "msg_profile_read", "msg_profile_read_level")
 KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
 
 
@@ -39,7 +39,6 @@ class msg_params(ctypes.Structure):
                 ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32),
                 ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32),
-                ("tune_warp_visit", ctypes.c_int32), ("tune_stage_from", ctypes.c_int32),
                 ("tune_low_threads", ctypes.c_int32)]
 
 
@@ -57,14 +56,12 @@ class SolverParams:
     coef: int = MSG_COEF_SERIES
     tune_block: int = 0      # launch shape only (no effect on results): 0 = library default
     tune_low_warps: int = 0
-    tune_warp_visit: int = 0
-    tune_stage_from: int = 0
     tune_low_threads: int = 0
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
-                          self.qoi, self.coef, self.tune_block, self.tune_low_warps, self.tune_warp_visit,
-                          self.tune_stage_from, self.tune_low_threads)
+                          self.qoi, self.coef, self.tune_block, self.tune_low_warps,
+                          self.tune_low_threads)
 
 
 _lib = None
@@ -107,6 +104,9 @@ def load(path: str | None = None):
     L.msg_launch_count.restype = i64
     L.msg_profile_enable.argtypes = [i32]
     L.msg_profile_enable.restype = i32
+    L.msg_profile_read_level.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
+    L.msg_profile_read_level.restype = i32
     L.msg_profile_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                                    ctypes.POINTER(dbl)]
     L.msg_profile_read.restype = i32
@@ -200,17 +200,28 @@ def msg_launch_count() -> int:
     return int(load().msg_launch_count())
 
 
-def msg_profile_enable(on: bool):
-    _check(load().msg_profile_enable(1 if on else 0))
+def msg_profile_enable(on: bool, stride: int = 1):
+    """Count every launch per kernel class and time a random 1/stride of them (on=False stops)."""
+    _check(load().msg_profile_enable(int(stride) if on else 0))
 
 
 def msg_profile_read(kernel_class) -> dict:
-    """{launches, ms, bytes, flops} summed over the recorded launches of one class."""
+    """{launches, ms, bytes, flops} of one class since msg_profile_enable: all launches
+    counted; ms, bytes and flops of the timed ones scaled to all launches."""
     k = KERNEL_CLASSES.index(kernel_class) if isinstance(kernel_class, str) else int(kernel_class)
     n = ctypes.c_int64()
     ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().msg_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
     return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+
+
+def msg_profile_read_level(kernel_class, level: int) -> dict:
+    """{timed, ms, bytes} over the timed launches of one class at one multigrid diagonal."""
+    k = KERNEL_CLASSES.index(kernel_class) if isinstance(kernel_class, str) else int(kernel_class)
+    n = ctypes.c_int64()
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(load().msg_profile_read_level(k, int(level), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return {"timed": n.value, "ms": ms.value, "bytes": by.value}
 
 
 # ------------------------------------------------------------ conveniences --
