@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time a few launch shapes on a sub-batch first (default: the library defaults)")
+    ap.add_argument("--no-autotune", action="store_true", help="(default; kept for old command lines)")
     ap.add_argument("--cpu-samples", type=int, default=0, help="oracle samples for the CPU baseline (0: one per core)")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
@@ -218,7 +220,7 @@ def ours(a, rank, world, local_rank):
     seed = 20190729
 
     tuned = None
-    if not a.no_autotune:
+    if a.autotune and not a.no_autotune:
         from paper_1907_12334_gb300 import autotune
 
         msg.msg_normals(seed, 0, S, M, xi)

@@ -76,7 +76,7 @@ typedef struct {
     int32_t precision;  /* MSG_PREC_* */
     int32_t qoi;        /* MSG_QOI_* */
     int32_t coef;       /* MSG_COEF_*: coarse-face coefficient */
-    int32_t tune_block; /* launch shape: threads per CTA of the visit kernels (0: 128; multiple of 32) */
+    int32_t tune_block; /* launch shape: threads per CTA of the visit kernels on mid-size grids (0: 128; multiple of 32; small grids use fewer, grids of 2^12+ cells twice as many) */
     int32_t tune_low_warps; /* launch shape: items per CTA of the low-diagonal kernel at one warp per item (0: 2; 1..8) */
     int32_t tune_low_threads; /* launch shape: threads per item there: 32, or 64/128 for one item per CTA (0: 32) */
 } msg_params;

@@ -1493,10 +1493,13 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             int64_t maxc = 0;
             for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k) maxc = std::max<int64_t>(maxc, h_segs[k].count);
             const dim3 g2((unsigned)maxc, (unsigned)dnseg[d]);  // x: sample in segment, y: segment
+            // threads per CTA: every grid of diagonal d has 2^(d+2) cells, 2^(d+1) points per
+            // colour; small grids get no idle warps, the big ones (d >= 10) twice the block
+            const int vb = d >= 10 ? std::min(2 * C.block, 1024) : std::min(C.block, std::max(32, 1 << (d + 1)));
             if (pre) {
-                k_pre<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+                k_pre<T><<<g2, vb, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
             } else {
-                k_post<T><<<g2, C.block, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
+                k_post<T><<<g2, vb, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
             }
             prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
