@@ -419,7 +419,7 @@ constexpr int kLowNodes = low_total();
 
 // phase kinds; a program word is kind | diagonal << 3, a resolved program
 // word (per class, empty phases dropped) is {kind | entries << 3, first entry}
-enum LowKind { LK_SMOOTH_RED = 0, LK_SMOOTH_BLACK, LK_RX, LK_RY, LK_PROL, LK_ZERO, LK_NKIND };
+enum LowKind { LK_SMOOTH_RED = 0, LK_SMOOTH_BLACK, LK_RESTRICT, LK_PROL, LK_NKIND };
 
 // Shape class of the triangle below diagonal dl of an item (pic, qic in 1..dl+1).
 __host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
@@ -433,15 +433,15 @@ struct LowDesc {
     int prog, nops;               // resolved program of the class (set per solve)
     int ngrid;
     int grid[kLowGrids];          // p | q << 4 | first node << 8, ordered by diagonal
-    int cnt[kDW + 1][LK_NKIND];   // entries of each (diagonal, kind); LK_ZERO: nodes
-    int off[kDW + 1][LK_NKIND];   // first entry in the table blob; LK_ZERO: first node
+    int cnt[kDW + 1][LK_NKIND];   // entries of each (diagonal, kind)
+    int off[kDW + 1][LK_NKIND];   // first entry in the table blob
 };
 
 // Table entries (uint2):
 //   smooth  x = c | W << 16                     node c of a grid with row stride W
-//   RX, RY  x = child c | parent c << 16,  y = W | flag << 16
-//           RX: child b = R_x r (flag: halved, the child has a y-parent too)
-//           RY: child b = R_y r (flag: b += R_y r / 2, the child has an x-parent)
+//   restrict  x = child c | x-parent c << 12 | has x-parent << 24 | has y-parent << 25
+//             y = y-parent c | child row stride Wc << 12   (x-parent stride 2 Wc - 1)
+//             one entry per interior node of a child grid on diagonal d-1
 //   prolong x = c | W << 12 | i odd << 20 | j odd << 21 | has x-child << 22 | has y-child << 23
 //           y = x-child node | y-child node << 16 (the coarse node left of / below (i,j))
 
@@ -453,11 +453,12 @@ __device__ __forceinline__ T low_res(const T* u, const T* b, const T* fx, const 
     return b[c] - Au;
 }
 
-// first entry of a phase for this lane (none for zeroing, or past the count)
+// first entry of a phase for this lane (none past the count)
 __device__ __forceinline__ uint2 low_first(const uint2* ent, uint2 op, int tid)
 {
     const int kind = op.x & 7, cnt = (int)(op.x >> 3);
-    return (kind != LK_ZERO && tid < cnt) ? ent[op.y + tid] : make_uint2(0u, 0u);
+    (void)kind;
+    return tid < cnt ? ent[op.y + tid] : make_uint2(0u, 0u);
 }
 
 template <class T>
@@ -469,22 +470,24 @@ __device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const 
     u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
 }
 
+// Eq. (2.3) for one child node: b = R_x r of the x-parent and/or R_y r of the
+// y-parent, averaged when it has both; the child's correction restarts from 0
+// (the recursion's first visit of the child follows every restriction).
 template <class T>
-__device__ __forceinline__ void low_rx(const T* u, T* b, const T* fx, const T* fy, uint2 e)
+__device__ __forceinline__ void low_restrict(T* u, T* b, const T* fx, const T* fy, uint2 e)
 {
-    const int cc = e.x & 0xFFFF, pc = e.x >> 16, W = e.y & 0xFFFF;
-    T v = T(0.25) * (low_res(u, b, fx, fy, pc - 1, W) + T(2) * low_res(u, b, fx, fy, pc, W) +
-                     low_res(u, b, fx, fy, pc + 1, W));
-    b[cc] = (e.y >> 16) ? T(0.5) * v : v;
-}
-
-template <class T>
-__device__ __forceinline__ void low_ry(const T* u, T* b, const T* fx, const T* fy, uint2 e)
-{
-    const int cc = e.x & 0xFFFF, pc = e.x >> 16, W = e.y & 0xFFFF;
-    T v = T(0.25) * (low_res(u, b, fx, fy, pc - W, W) + T(2) * low_res(u, b, fx, fy, pc, W) +
-                     low_res(u, b, fx, fy, pc + W, W));
-    b[cc] = (e.y >> 16) ? b[cc] + T(0.5) * v : v;
+    const int cc = e.x & 0xFFF, px = (e.x >> 12) & 0xFFF, py = e.y & 0xFFF;
+    const bool hx = (e.x >> 24) & 1, hy = (e.x >> 25) & 1;
+    const int Wc = e.y >> 12, Wx = 2 * Wc - 1;
+    T vx = T(0), vy = T(0);
+    if (hx)
+        vx = T(0.25) * (low_res(u, b, fx, fy, px - 1, Wx) + T(2) * low_res(u, b, fx, fy, px, Wx) +
+                        low_res(u, b, fx, fy, px + 1, Wx));
+    if (hy)
+        vy = T(0.25) * (low_res(u, b, fx, fy, py - Wc, Wc) + T(2) * low_res(u, b, fx, fy, py, Wc) +
+                        low_res(u, b, fx, fy, py + Wc, Wc));
+    b[cc] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+    u[cc] = T(0);
 }
 
 template <class T>
@@ -574,17 +577,12 @@ __global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su
             const uint2 e1 = low_first(ent, op1, tid);
             const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
             if (tid < cnt) {
-                if (kind == LK_ZERO) {
-                    for (int k = tid; k < cnt; k += NT) u[off + k] = T(0);
-                } else if (kind <= LK_SMOOTH_BLACK) {
+                if (kind <= LK_SMOOTH_BLACK) {
                     low_smooth(u, b, fx, fy, e);
                     for (int k = tid + NT; k < cnt; k += NT) low_smooth(u, b, fx, fy, ent[off + k]);
-                } else if (kind == LK_RX) {
-                    low_rx(u, b, fx, fy, e);
-                    for (int k = tid + NT; k < cnt; k += NT) low_rx(u, b, fx, fy, ent[off + k]);
-                } else if (kind == LK_RY) {
-                    low_ry(u, b, fx, fy, e);
-                    for (int k = tid + NT; k < cnt; k += NT) low_ry(u, b, fx, fy, ent[off + k]);
+                } else if (kind == LK_RESTRICT) {
+                    low_restrict(u, b, fx, fy, e);
+                    for (int k = tid + NT; k < cnt; k += NT) low_restrict(u, b, fx, fy, ent[off + k]);
                 } else {
                     low_prol(u, fx, fy, e, omega);
                     for (int k = tid + NT; k < cnt; k += NT) low_prol(u, fx, fy, ent[off + k], omega);
@@ -854,8 +852,7 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
     int toff[kDW + 3][kDW + 3];
     int nn = 0;
     auto exists = [&](int p, int q) { return p >= 1 && q >= 1 && p <= pic && q <= qic && p + q - 2 <= dl; };
-    for (int d = 0; d <= dl; ++d) {
-        D.off[d][LK_ZERO] = nn;
+    for (int d = 0; d <= dl; ++d)
         for (int p = 1; p <= d + 1; ++p) {
             const int q = d + 2 - p;
             if (!exists(p, q)) continue;
@@ -863,8 +860,6 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
             D.grid[D.ngrid++] = p | q << 4 | nn << 8;
             nn += low_nodes(p, q);
         }
-        D.cnt[d][LK_ZERO] = nn - D.off[d][LK_ZERO];
-    }
     D.nn = nn;
     for (int d = 0; d <= dl; ++d) {
         for (int colour = 0; colour < 2; ++colour) {  // red: (i + j) even
@@ -881,35 +876,25 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
             D.cnt[d][LK_SMOOTH_RED + colour] = (int)ent.size() - D.off[d][LK_SMOOTH_RED + colour];
         }
         if (d == 0) continue;
-        // Eq. (2.3): x-children (p-1, q) take R_x, halved when they also have the
-        // y-parent (p-1, q+1); y-children (p, q-1) add R_y/2 when they also have
-        // the x-parent (p+1, q-1), else take R_y
-        D.off[d][LK_RX] = (int)ent.size();
-        for (int p = 2; p <= d + 1; ++p) {
-            const int q = d + 2 - p;
+        // Eq. (2.3), one entry per interior node of each child (p, q) on diagonal
+        // d-1: R_x from the x-parent (p+1, q), R_y from the y-parent (p, q+1)
+        D.off[d][LK_RESTRICT] = (int)ent.size();
+        for (int p = 1; p <= d; ++p) {
+            const int q = d + 1 - p;
             if (!exists(p, q)) continue;
-            const int nx = 1 << p, ny = 1 << q, W = nx + 1, Wc = (nx >> 1) + 1;
-            const uint32_t half = q < qic ? 1u : 0u;
+            const bool hx = exists(p + 1, q), hy = exists(p, q + 1);
+            if (!hx && !hy) continue;  // only in classes no item has (pic + qic < dl + 2)
+            const int nx = 1 << p, ny = 1 << q, Wc = nx + 1, Wx = 2 * nx + 1;
             for (int j = 1; j < ny; ++j)
-                for (int ic = 1; ic < (nx >> 1); ++ic)
-                    ent.push_back(make_uint2((uint32_t)(toff[p - 1][q] + j * Wc + ic) |
-                                                 (uint32_t)(toff[p][q] + j * W + 2 * ic) << 16,
-                                             (uint32_t)W | half << 16));
+                for (int i = 1; i < nx; ++i) {
+                    const uint32_t px = hx ? (uint32_t)(toff[p + 1][q] + j * Wx + 2 * i) : 0u;
+                    const uint32_t py = hy ? (uint32_t)(toff[p][q + 1] + 2 * j * Wc + i) : 0u;
+                    ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * Wc + i) | px << 12 | (uint32_t)hx << 24 |
+                                                 (uint32_t)hy << 25,
+                                             py | (uint32_t)Wc << 12));
+                }
         }
-        D.cnt[d][LK_RX] = (int)ent.size() - D.off[d][LK_RX];
-        D.off[d][LK_RY] = (int)ent.size();
-        for (int p = 1; p <= d + 1; ++p) {
-            const int q = d + 2 - p;
-            if (q < 2 || !exists(p, q)) continue;
-            const int nx = 1 << p, ny = 1 << q, W = nx + 1;
-            const uint32_t both = p < pic ? 1u : 0u;
-            for (int jc = 1; jc < (ny >> 1); ++jc)
-                for (int i = 1; i < nx; ++i)
-                    ent.push_back(make_uint2((uint32_t)(toff[p][q - 1] + jc * W + i) |
-                                                 (uint32_t)(toff[p][q] + 2 * jc * W + i) << 16,
-                                             (uint32_t)W | both << 16));
-        }
-        D.cnt[d][LK_RY] = (int)ent.size() - D.off[d][LK_RY];
+        D.cnt[d][LK_RESTRICT] = (int)ent.size() - D.off[d][LK_RESTRICT];
         // Eq. (2.4)/(2.5): linear prolongation from each child, kappa-weighted
         D.off[d][LK_PROL] = (int)ent.size();
         for (int p = 1; p <= d + 1; ++p) {
@@ -945,19 +930,19 @@ static const LowTables& low_tables()
 }
 
 // Algorithm 1 below diagonal dl as a flat program (the recursion unrolled): the
-// visit of diagonal d zeroes it when it is the first of its parent's mu visits,
-// smooths nu1 times, restricts to diagonal d-1, recurses mu times, prolongs and
-// smooths nu2 times; diagonal 0 is solved exactly (one unknown).  The top is
-// not zeroed: the kernel starts every item from u = 0.
-static void low_program_rec(int d, bool zero, const msg_params& prm, std::vector<int>& prog)
+// visit of diagonal d smooths nu1 times, restricts to diagonal d-1 (which also
+// restarts the correction there from zero for the first of the mu visits),
+// recurses mu times, prolongs and smooths nu2 times.  Diagonal 0 is solved
+// exactly (one unknown, u = b / A); its b does not change between the mu
+// visits of one parent visit, so the repeats, which would write the same
+// value, are left out.  The kernel starts every item from u = 0.
+static void low_program_rec(int d, const msg_params& prm, std::vector<int>& prog)
 {
     auto emit = [&](int kind, int dd) { prog.push_back(kind | dd << 3); };
     if (d == 0) { emit(LK_SMOOTH_RED, 0); return; }
-    if (zero) emit(LK_ZERO, d);
     for (int s = 0; s < prm.nu1; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
-    emit(LK_RX, d);
-    emit(LK_RY, d);
-    for (int k = 0; k < prm.mu; ++k) low_program_rec(d - 1, k == 0, prm, prog);
+    emit(LK_RESTRICT, d);
+    for (int k = 0; k < (d == 1 ? 1 : prm.mu); ++k) low_program_rec(d - 1, prm, prog);
     emit(LK_PROL, d);
     for (int s = 0; s < prm.nu2; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
 }
@@ -965,7 +950,7 @@ static void low_program_rec(int d, bool zero, const msg_params& prm, std::vector
 static std::vector<int> low_program(int dl, const msg_params& prm)
 {
     std::vector<int> prog;
-    low_program_rec(dl, false, prm, prog);
+    low_program_rec(dl, prm, prog);
     return prog;
 }
 
