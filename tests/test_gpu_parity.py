@@ -178,6 +178,20 @@ def test_result_independent_of_batch_mix(msg):
     assert np.array_equal(Qmix[16:26], Qalone)
 
 
+@pytest.mark.parametrize("shape", [dict(tune_low_warps=3), dict(tune_low_threads=64), dict(tune_low_threads=128),
+                                   dict(tune_block=64, tune_low_warps=1), dict(tune_block=256, tune_low_warps=4)])
+def test_launch_shapes_do_not_change_results(msg, shape):
+    """Launch shapes only regroup independent per-node updates: bit-exact results.
+    The batch mixes shapes (items of several low-diagonal classes in one CTA)
+    and has an item count that leaves warps of the last CTA idle."""
+    shapes = SHAPES_SMALL + [(2, 6), (6, 2), (5, 4)]
+    Zs = oracle_fields(shapes, seed=5)
+    ref = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300)
+    got = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300, **shape)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
 # ------------------------------------------------------------------ (a14) --
 
 def test_mimc_differences_bit_exact(msg):
