@@ -223,32 +223,50 @@ __device__ void cta_coarsest(const G& grp, const GView<T>& g)
 }
 
 // Full-weighting restriction of the residual of g (Eq. (2.3)): R_x r into the
-// x-child's bx (if cxb != nullptr), R_y r into the y-child's by.
+// x-child's bx (if cxb != nullptr), R_y r into the y-child's by.  The residual
+// is formed once per interior node into shared memory `sr` (capacity `band`
+// nodes, at least 3 rows) band by band: a band of B rows (B odd) starting at
+// an odd row a holds rows a..a+B-1; it restricts its rows but the last in x
+// (the last band all of them) and the coarse rows jc with 2jc-1 >= a and
+// 2jc+1 <= a+B-1 in y; the next band starts at a+B-1.
 template <class T, class G>
-__device__ void cta_restrict(const G& grp, const GView<T>& g, T* cxb, T* cyb)
+__device__ void cta_restrict(const G& grp, const GView<T>& g, T* cxb, T* cyb, T* sr, int band)
 {
-    const int W = g.nx + 1;
-    if (cxb) {  // child (p-1,q): nx/2 = 2^shc cells, same rows (slot ic = 0 is the boundary)
-        const int ncx = g.nx >> 1, Wc = ncx + 1, shc = __ffs(ncx) - 1, n = (g.ny - 1) << shc;
-        for (int k = grp.tid; k < n; k += grp.n) {
-            const int ic = k & (ncx - 1), j = 1 + (k >> shc);
-            if (ic == 0) continue;
-            const int c = j * W + 2 * ic;
-            T v = T(0.25) * (res_at(g, c - 1, W) + T(2) * res_at(g, c, W) + res_at(g, c + 1, W));
-            cxb[j * Wc + ic] = v;
-        }
-    }
-    if (cyb) {  // child (p,q-1): same columns, ny/2 cells (slot i = 0 is the boundary)
-        const int ncy = g.ny >> 1, sh = __ffs(g.nx) - 1, n = (ncy - 1) << sh;
-        for (int k = grp.tid; k < n; k += grp.n) {
-            const int i = k & (g.nx - 1), jc = 1 + (k >> sh);
+    const int W = g.nx + 1, sh = __ffs(g.nx) - 1, last = g.ny - 1;
+    int B = band / W;
+    if (B >= last) B = last;  // one band holds every interior row
+    else B = (B - 1) | 1;     // odd, >= 3 (band >= 3 W)
+    for (int a = 1; a <= last; a += max(B - 1, 1)) {
+        const int e = min(a + B - 1, last);  // last row of the band
+        const int nr = (e - a + 1) << sh;
+        for (int k = grp.tid; k < nr; k += grp.n) {
+            const int i = k & (g.nx - 1), j = a + (k >> sh);
             if (i == 0) continue;
-            const int c = 2 * jc * W + i;
-            T v = T(0.25) * (res_at(g, c - W, W) + T(2) * res_at(g, c, W) + res_at(g, c + W, W));
-            cyb[jc * W + i] = v;
+            sr[(j - a) * W + i] = res_at(g, j * W + i, W);
         }
+        grp.sync();
+        if (cxb) {  // child (p-1,q): nx/2 = 2^shc cells, same rows (slot ic = 0 is the boundary)
+            const int ncx = g.nx >> 1, Wc = ncx + 1, shc = sh - 1;
+            const int ex = (e == last) ? e : e - 1, n = (ex - a + 1) << shc;
+            for (int k = grp.tid; k < n; k += grp.n) {
+                const int ic = k & (ncx - 1), j = a + (k >> shc);
+                if (ic == 0) continue;
+                const int r = (j - a) * W + 2 * ic;
+                cxb[j * Wc + ic] = T(0.25) * (sr[r - 1] + T(2) * sr[r] + sr[r + 1]);
+            }
+        }
+        if (cyb) {  // child (p,q-1): same columns, coarse row jc from fine rows 2jc-1..2jc+1
+            const int j0 = (a + 1) >> 1, j1 = (e - 1) >> 1, n = max(j1 - j0 + 1, 0) << sh;
+            for (int k = grp.tid; k < n; k += grp.n) {
+                const int i = k & (g.nx - 1), jc = j0 + (k >> sh);
+                if (i == 0) continue;
+                const int r = (2 * jc - a) * W + i;
+                cyb[jc * W + i] = T(0.25) * (sr[r - W] + T(2) * sr[r] + sr[r + W]);
+            }
+        }
+        grp.sync();
+        if (e == last) break;
     }
-    grp.sync();
 }
 
 // Coarse-grid correction (Eq. (2.4) with linear P and the weights of Eq. (2.5)):
@@ -317,7 +335,7 @@ __device__ __forceinline__ GView<T> view_of(const Hier<T>& h, int p, int q)
 
 // Visit halves of Algorithm 1 on one grid (p,q) of an item's hierarchy.
 template <class T, class G>
-__device__ void visit_pre(const G& grp, const Hier<T>& h, int p, int q, int zero_init, int nu1)
+__device__ void visit_pre(const G& grp, const Hier<T>& h, int p, int q, int zero_init, int nu1, T* sr, int band)
 {
     GView<T> g = view_of(h, p, q);
     if (p == 1 && q == 1) { cta_coarsest(grp, g); return; }
@@ -325,7 +343,7 @@ __device__ void visit_pre(const G& grp, const Hier<T>& h, int p, int q, int zero
     cta_smooth(grp, g, nu1);
     T* cxb = (p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
     T* cyb = (q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    cta_restrict(grp, g, cxb, cyb);
+    cta_restrict(grp, g, cxb, cyb, sr, band);
 }
 
 template <class T, class G>
@@ -368,12 +386,13 @@ __device__ __forceinline__ Hier<T> hier_of(const DevCtx& cx, const TaskRef& t, T
 }
 
 template <class T>
-__global__ void k_pre(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
+__global__ void k_pre(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1, int band)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // `band` residual nodes
     TaskRef t;
     if (!resolve_2d(cx, t)) return;
     Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    visit_pre(CtaGroup(), h, t.seg->p, t.seg->q, zero_init, nu1);
+    visit_pre(CtaGroup(), h, t.seg->p, t.seg->q, zero_init, nu1, (T*)smem_raw, band);
 }
 
 template <class T>
@@ -1172,6 +1191,7 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
 constexpr int kThreads = 256;
 constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory of one CTA
 constexpr int kVisitThreads = 128;       // threads per CTA of the PRE/POST visit kernels (default)
+constexpr int kBandNodes = 4096;         // residual band of the restriction in shared memory (nodes)
 constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-resident, one launch
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
@@ -1482,7 +1502,14 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             // colour; small grids get no idle warps, the big ones (d >= 10) twice the block
             const int vb = d >= 10 ? std::min(2 * C.block, 1024) : std::min(C.block, std::max(32, 1 << (d + 1)));
             if (pre) {
-                k_pre<T><<<g2, vb, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
+                // residual band of the restriction: the whole grid when it has at most
+                // kBandNodes nodes, else bands of at least 3 rows
+                int band = 0;
+                for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k) {
+                    const int W = (1 << h_segs[k].p) + 1, n = W * ((1 << h_segs[k].q) + 1);
+                    band = std::max(band, std::min(n, std::max(kBandNodes, 3 * W)));
+                }
+                k_pre<T><<<g2, vb, sizeof(T) * band, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1, band);
             } else {
                 k_post<T><<<g2, vb, 0, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
             }
@@ -1592,6 +1619,9 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         // the sources are host vectors: finish the copies before they go out of scope
         MSG_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    // the residual band: 3 rows of a 2^12-cell-wide grid at most
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(T) * std::max(kBandNodes, 3 * ((1 << 12) + 1)))));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * 4 * kLowNodes * C.low_warps)));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
