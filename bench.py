@@ -28,8 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSG samples/s at QoI rel err <=1e-8 vs plain FP64"
-# every launch is counted; a random 1/PROFILE_STRIDE of each kernel class's launches is timed
-# with CUDA events inside the timed region (timing every one costs ~10% of the step on the host)
+# every launch is counted; a random 1/PROFILE_STRIDE of the launches of the cycle kernel classes
+# (all launches of the others) is timed with CUDA events inside the timed region (timing every
+# launch costs ~10% of the step on the host)
 PROFILE_STRIDE = 16
 
 

@@ -177,9 +177,10 @@ int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t p0, int32_
 /*                                                                          */
 /* msg_launch_count: number of CUDA kernels this library has launched in this */
 /* process.  msg_profile_enable(n), n >= 1, clears the records, counts every  */
-/* launch of each kernel class and times a random 1/n of them with CUDA       */
-/* events on their own streams (0 stops; n > 1 keeps the event overhead off   */
-/* most launches).  msg_profile_read returns, for one kernel class, the       */
+/* launch of each kernel class and times a random 1/n of the launches of the  */
+/* cycle classes (PRE, POST, LOW, RESIDUAL, UPDATE) and every launch of the   */
+/* others with CUDA events on their own streams (0 stops; n > 1 keeps the     */
+/* event overhead off most launches).  msg_profile_read returns, for one kernel class, the       */
 /* launches counted and the event-timed milliseconds, algorithmic bytes and   */
 /* flops (the compulsory traffic/work per launch as defined in the design     */
 /* notes) of the timed ones, scaled by launches / timed launches (exact for   */

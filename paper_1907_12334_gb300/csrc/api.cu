@@ -61,7 +61,10 @@ void prof_begin(int cls, cudaStream_t st)
     const int n = g_prof.stride.load(std::memory_order_relaxed);
     if (n <= 0) return;
     g_prof.count[cls].fetch_add(1, std::memory_order_relaxed);
-    if (!sample_one_in(n)) return;
+    // the cycle's classes launch thousands of times per solve and are sampled;
+    // the once-per-step or per-stage classes are always timed
+    const bool cycle_class = cls == K_PRE || cls == K_POST || cls == K_LOW || cls == K_RESIDUAL || cls == K_UPDATE;
+    if (cycle_class && !sample_one_in(n)) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.take();
     cudaEventRecord(e, st);
