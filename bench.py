@@ -349,7 +349,8 @@ def ours(a, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * elapsed / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": workload_name(a), "S_per_gpu": S, "P": P, "Q": Q, "M": M, "eps": a.eps,
                        "omega": a.omega, "l2": "inputs larger than L2 (Z alone is 8.6 GB per step)",
                        "converged_fraction": conv_frac, "launch_shapes": tuned},
