@@ -71,7 +71,9 @@ def test_workspace_bytes_host_logic(lib):
 @pytest.mark.parametrize("PQ,kw", [([[0, 3]], {}), ([[3, 13]], {}), ([[3, 3]], {"mu": 0}),
                                     ([[3, 3]], {"max_cycles": 0}), ([[3, 3]], {"omega": 0.0}),
                                     ([[3, 3]], {"precision": 7}), ([[3, 3]], {"qoi": 9}),
-                                    ([[3, 3]], {"eps": float("nan")})])
+                                    ([[3, 3]], {"eps": float("nan")}), ([[3, 3]], {"nu1": 65}),
+                                    ([[3, 3]], {"tune_block": 48}), ([[3, 3]], {"tune_low_warps": 9}),
+                                    ([[3, 3]], {"tune_low_threads": 16})])
 def test_invalid_arguments_rejected_on_host(lib, PQ, kw):
     assert _ws(PQ, **kw) == 0
     assert lib.msg_last_error() != b""
@@ -100,3 +102,18 @@ def test_mimc_rejects_bad_indices(lib):
     rc = lib.mimc_differences(L.ctypes.data_as(ctypes.c_void_p), 1, 1, 1, ctypes.c_void_p(8), None, 0, 0,
                               ctypes.c_void_p(8), None, None)
     assert rc == msg.MSG_ERR_INVALID
+
+
+def test_profiling_api_host_logic(lib):
+    """Counting and sampled timing: argument checks and empty reads need no GPU."""
+    assert lib.msg_profile_enable(-1) == msg.MSG_ERR_INVALID
+    msg.msg_profile_enable(True, stride=4)
+    r = msg.msg_profile_read("PRE")
+    assert r == {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0}
+    assert msg.msg_profile_read_level("LOW", 4) == {"timed": 0, "ms": 0.0, "bytes": 0.0}
+    n = ctypes.c_int64()
+    d = ctypes.c_double()
+    assert lib.msg_profile_read_level(2, -1, ctypes.byref(n), ctypes.byref(d), ctypes.byref(d)) == msg.MSG_ERR_INVALID
+    assert lib.msg_profile_read(99, ctypes.byref(n), ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == \
+        msg.MSG_ERR_INVALID
+    msg.msg_profile_enable(False)
