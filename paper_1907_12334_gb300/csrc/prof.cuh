@@ -8,7 +8,7 @@ namespace msg {
 enum KernelClass {
     K_PRE = 0,   // PRE half of a visit above the cut (zero, nu1 sweeps, restriction)
     K_POST,      // POST half of a visit above the cut (prolongation, nu2 sweeps)
-    K_LOW,       // whole recursion at and below the cut, one CTA per item
+    K_LOW,       // whole recursion at and below the cut, one warp per item (k_low)
     K_RESIDUAL,  // FP64 residual + convergence decision
     K_UPDATE,    // FP64 update u += e
     K_INTERP,    // FMSG cubic interpolation

@@ -1199,7 +1199,7 @@ constexpr int kThreads = 256;
 constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory of one CTA
 constexpr int kVisitThreads = 128;       // threads per CTA of the PRE/POST visit kernels (default)
 constexpr int kBandNodes = 4096;         // residual band of the restriction in shared memory (nodes)
-constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run warp-resident, one launch
+constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run in one k_low launch
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
 struct Pinned {
