@@ -180,6 +180,26 @@ def reference_arm(a, rank, world):
 
 # --------------------------------------------------------------- our arm --
 
+def step_offset(k, world, rank, S):
+    """First sample of rank `rank`'s batch in step k: steps and ranks tile the
+    sample stream, so no two batches of a run share a sample."""
+    return (k * world + rank) * S
+
+
+def job_totals(elapsed, converged, dist=None, device="cpu"):
+    """Whole-job figures: the slowest rank's time and the converged samples of all
+    ranks (replicas only: these two reductions are the run's only collectives)."""
+    if dist is None:
+        return float(elapsed), int(converged)
+    import torch
+
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    c = torch.tensor([int(converged)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def ours(a, rank, world, local_rank):
     import torch
 
@@ -230,7 +250,7 @@ def ours(a, rank, world, local_rank):
         tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps}
 
     def step(k):
-        s0 = (k * world + rank) * S
+        s0 = step_offset(k, world, rank, S)
         msg.msg_normals(seed, s0, S, M, xi)
         msg.sample_field(prep, npts, M, gemm, xi, Z)
         msg.msg_solve_batch(PQ, prm, Z, Qout, status, cycles, relres, ws)
@@ -263,11 +283,8 @@ def ours(a, rank, world, local_rank):
     prof = {c: msg.msg_profile_read(c) for c in msg.KERNEL_CLASSES}
     msg.msg_profile_enable(False)
     st_last = status.cpu().numpy()
-    conv_frac = float((st_last == 0).mean())
-    if dist:
-        t = torch.tensor([elapsed], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed, conv_all = job_totals(elapsed, int((st_last == 0).sum()), tdist if dist else None, dev)
+    conv_frac = conv_all / (world * S)
     value = world * S * a.steps * conv_frac / elapsed
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
