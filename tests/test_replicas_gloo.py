@@ -52,7 +52,7 @@ def _free_port():
 
 def test_job_totals_max_time_and_summed_count_over_two_gloo_ranks():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
