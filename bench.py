@@ -56,6 +56,9 @@ def parse():
                     help="time a few launch shapes on a sub-batch first (default: the library defaults)")
     ap.add_argument("--no-autotune", action="store_true", help="(default; kept for old command lines)")
     ap.add_argument("--cpu-samples", type=int, default=0, help="oracle samples for the CPU baseline (0: one per core)")
+    ap.add_argument("--plain-fp64", type=int, default=0, metavar="N",
+                    help="also time N samples solved one at a time with FP64 cycles (the per-sample "
+                         "FP64 GPU path) and report it beside the batched mixed path")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -313,6 +316,35 @@ def ours(a, rank, world, local_rank):
     e2e_conv = float((h_st.numpy() == 0).mean())
     e2e_val = None if a.no_e2e else world * S * a.steps * e2e_conv / e2e_s
 
+    # ---- optional: the per-sample FP64 GPU path (one sample per call, FP64 cycles)
+    plain = None
+    if a.plain_fp64 > 0 and rank == 0:
+        prm64 = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega, precision=msg.MSG_PREC_FP64)
+        pq1 = PQ[:1]
+        ws1 = torch.empty(msg.msg_workspace_bytes(pq1, prm64), dtype=torch.uint8, device=dev)
+        xi1, Z1 = xi[:1], Z[:1]
+        Q1, st1 = Qout[:P * Q], status[:1]
+        c1, r1 = cycles[:P * Q], relres[:P * Q]
+
+        def one(s):
+            msg.msg_normals(seed, s, 1, M, xi1)
+            msg.sample_field(prep, npts, M, gemm, xi1, Z1)
+            msg.msg_solve_batch(pq1, prm64, Z1, Q1, st1, c1, r1, ws1)
+
+        one(0)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        nconv = 0
+        for s in range(a.plain_fp64):
+            one(s)
+            nconv += int(st1.item() == 0)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1000.0
+        plain = {"value": nconv / t, "unit": "samples/s", "samples": a.plain_fp64, "converged": nconv,
+                 "batched_mixed_over_plain": value / (nconv / t) if nconv else None}
+
     # ---- optional: one untimed step with every launch timed, per multigrid diagonal
     if a.profile_levels and rank == 0:
         msg.msg_profile_enable(True, stride=1)
@@ -379,6 +411,7 @@ def ours(a, rank, world, local_rank):
             "kernel_profile": {c: {"launches": v["launches"], "ms": round(v["ms"], 3)} for c, v in prof.items()
                                if v["launches"]},
             "qoi_check": check,
+            **({"plain_fp64_gpu": plain} if plain else {}),
         }
         print(json.dumps(line), flush=True)
 
