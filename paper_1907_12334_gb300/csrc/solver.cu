@@ -144,13 +144,17 @@ __device__ __forceinline__ bool resolve_2d(const DevCtx& cx, TaskRef& t)
 // from 1/x; the arguments, sums of a/h^2 > 0, are never subnormal), which is
 // enough because those cycles only produce a correction and the FP64 residual
 // decides convergence; exact division in FP64.
-__device__ __forceinline__ float rcp_of(float x)
+__host__ __device__ __forceinline__ float rcp_of(float x)
 {
+#ifdef __CUDA_ARCH__
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+#else
+    return 1.0f / x;  // host builds (table checks) only
+#endif
 }
-__device__ __forceinline__ double rcp_of(double x) { return 1.0 / x; }
+__host__ __device__ __forceinline__ double rcp_of(double x) { return 1.0 / x; }
 
 template <class T>
 struct GView {
@@ -415,11 +419,15 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
 //
 // Diagonals d <= kDW of an item's hierarchy are visited 2^(L-d) times per
 // cycle (Algorithm 1 with mu = 2) but hold only a few hundred unknowns, so
-// their cost is the latency of the dependent phases, not bandwidth.  One
-// thread group (a warp, or a CTA of 64/128 threads) owns one item: u, b and
-// the two face-coefficient arrays of every grid with p + q <= kDW + 2 live in
-// shared memory as four planes of the same node layout (grids ordered by
-// diagonal), and the mu-cycles run as a flat program of phases.
+// their cost is the latency of the dependent phases, not bandwidth, and the
+// throughput comes from items in flight.  One thread group (a warp, or a CTA
+// of 64/128 threads) owns one item, whose grids with p + q <= kDW + 2 live in
+// shared memory in four compact planes (grids ordered by diagonal):
+//   u   every node of every grid (the boundary stays zero),
+//   b   interior nodes only,
+//   fx  the x-faces (i+1/2, j) of interior rows, fy the y-faces (i, j+1/2) of
+//       interior columns: exactly the coefficients a stencil reads.
+// The mu-cycles run as a flat program of phases.
 //
 // The program is the recursion of Algorithm 1 unrolled on the host: a list
 // of (phase kind, diagonal) words.  What a phase touches is a table of node
@@ -434,14 +442,20 @@ constexpr int kLowGrids = (kDW + 1) * (kDW + 2) / 2;
 constexpr int kLowClasses = 55;  // sum over dl = 0..kDW of (dl + 1)^2
 
 __host__ __device__ constexpr int low_nodes(int p, int q) { return ((1 << p) + 1) * ((1 << q) + 1); }
-__host__ __device__ constexpr int low_total()
+// values one grid keeps in the four planes: nodes, interior nodes, x-faces, y-faces
+__host__ __device__ constexpr int low_values(int p, int q)
+{
+    return low_nodes(p, q) + ((1 << p) - 1) * ((1 << q) - 1) + (1 << p) * ((1 << q) - 1) +
+           ((1 << p) - 1) * (1 << q);
+}
+__host__ __device__ constexpr int low_slot()
 {
     int o = 0;
     for (int p = 1; p <= kDW + 1; ++p)
-        for (int q = 1; q <= kDW + 2 - p; ++q) o += low_nodes(p, q);
+        for (int q = 1; q <= kDW + 2 - p; ++q) o += low_values(p, q);
     return o;
 }
-constexpr int kLowNodes = low_total();
+constexpr int kLowSlot = low_slot();  // values per item (the full triangle)
 
 // phase kinds; a program word is kind | diagonal << 3, a resolved program
 // word (per class, empty phases dropped) is {kind | entries << 3, first entry}
@@ -454,81 +468,102 @@ __host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
 }
 
 struct LowDesc {
-    int nn;                       // nodes of the class's grids: the size of each plane
+    int nu, nb, nfx, nfy;         // sizes of the class's four planes
     int dl;
     int prog, nops;               // resolved program of the class (set per solve)
     int ngrid;
-    int grid[kLowGrids];          // p | q << 4 | first node << 8, ordered by diagonal
+    int grid[kLowGrids];          // p | q << 4 | first node in u << 8, ordered by diagonal
+    int gb[kLowGrids];            // first interior node of the grid in b
+    int gx[kLowGrids];            // first x-face of the grid in fx
+    int gy[kLowGrids];            // first y-face of the grid in fy
     int cnt[kDW + 1][LK_NKIND];   // entries of each (diagonal, kind)
-    int off[kDW + 1][LK_NKIND];   // first entry in the table blob
+    int off[kDW + 1][LK_NKIND];   // first table word (uint2) of the phase
 };
 
-// Table entries (uint2):
-//   smooth  x = c | W << 16                     node c of a grid with row stride W
-//   restrict  x = child c | x-parent c << 12 | has x-parent << 24 | has y-parent << 25
-//             y = y-parent c | child row stride Wc << 12   (x-parent stride 2 Wc - 1)
-//             one entry per interior node of a child grid on diagonal d-1
-//   prolong x = c | W << 12 | i odd << 20 | j odd << 21 | has x-child << 22 | has y-child << 23
-//           y = x-child node | y-child node << 16 (the coarse node left of / below (i,j))
+// Where an interior node (i, j) of a grid with row stride W = nx + 1 sits:
+//   u: first + j W + i;  b: gb + (j-1)(W-2) + (i-1)
+//   x-face (i+1/2, j): gx + (j-1)(W-1) + i;  y-face (i, j+1/2): gy + j (W-2) + (i-1)
+// so its stencil reads fx[x-1], fx[x] (west, east) and fy[y], fy[y + W-2]
+// (south, north) with x = its east face and y = its south face.
+//
+// Table entries:
+//   smooth   uint2  x = u | b << 10 | W << 20       y = x-face | y-face << 16
+//   restrict 2 uint2, one per interior node of a child grid on diagonal d-1:
+//            x = child u | child b << 10 | Wc << 20 | has x-parent << 26 | has y-parent << 27
+//            y = x-parent centre u | b << 10 | x-face << 20      (x-parent stride 2 Wc - 1)
+//            z = x-parent centre y-face | y-parent centre u << 10 | b << 20
+//            w = y-parent centre x-face | y-face << 10             (y-parent stride Wc)
+//   prolong  uint2  x = u | W << 10 | i odd << 16 | j odd << 17 | has x-child << 18 |
+//                       has y-child << 19 | x-face << 20
+//                   y = x-child node | y-child node << 10 | y-face << 20
+//            (the child nodes are the coarse u nodes left of / below (i, j))
 
+// Residual b - A u at one node (u index c, b index bi, east x-face xf, south y-face yf).
 template <class T>
-__device__ __forceinline__ T low_res(const T* u, const T* b, const T* fx, const T* fy, int c, int W)
+__host__ __device__ __forceinline__ T low_res(const T* u, const T* b, const T* fx, const T* fy, int c, int bi, int xf,
+                                              int yf, int W)
 {
-    T aw = fx[c - 1], ae = fx[c], as = fy[c - W], an = fy[c];
+    T aw = fx[xf - 1], ae = fx[xf], as = fy[yf], an = fy[yf + W - 2];
     T Au = (aw + ae + as + an) * u[c] - (aw * u[c - 1] + ae * u[c + 1]) - (as * u[c - W] + an * u[c + W]);
-    return b[c] - Au;
+    return b[bi] - Au;
 }
 
-// first entry of a phase for this lane (none past the count)
+// first table word of a phase for this lane (none past the count)
 __device__ __forceinline__ uint2 low_first(const uint2* ent, uint2 op, int tid)
 {
     const int kind = op.x & 7, cnt = (int)(op.x >> 3);
-    (void)kind;
-    return tid < cnt ? ent[op.y + tid] : make_uint2(0u, 0u);
+    return tid < cnt ? ent[op.y + (kind == LK_RESTRICT ? 2 * tid : tid)] : make_uint2(0u, 0u);
 }
 
 template <class T>
-__device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint2 e)
+__host__ __device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint2 e)
 {
-    const int c = e.x & 0xFFFF, W = e.x >> 16;
-    T aw = fx[c - 1], ae = fx[c], as = fy[c - W], an = fy[c];
+    const int c = e.x & 0x3FF, bi = (e.x >> 10) & 0x3FF, W = e.x >> 20, xf = e.y & 0xFFFF, yf = e.y >> 16;
+    T aw = fx[xf - 1], ae = fx[xf], as = fy[yf], an = fy[yf + W - 2];
     T nb = (aw * u[c - 1] + ae * u[c + 1]) + (as * u[c - W] + an * u[c + W]);
-    u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
+    u[c] = (b[bi] + nb) * rcp_of(aw + ae + as + an);
 }
 
 // Eq. (2.3) for one child node: b = R_x r of the x-parent and/or R_y r of the
 // y-parent, averaged when it has both; the child's correction restarts from 0
 // (the recursion's first visit of the child follows every restriction).
+// The three x-parent nodes are neighbours in one row (every index +-1), the
+// three y-parent nodes in one column (u +-Wc, b and y-face +-(Wc-2), x-face +-(Wc-1)).
 template <class T>
-__device__ __forceinline__ void low_restrict(T* u, T* b, const T* fx, const T* fy, uint2 e)
+__host__ __device__ __forceinline__ void low_restrict(T* u, T* b, const T* fx, const T* fy, uint2 e, uint2 f)
 {
-    const int cc = e.x & 0xFFF, px = (e.x >> 12) & 0xFFF, py = e.y & 0xFFF;
-    const bool hx = (e.x >> 24) & 1, hy = (e.x >> 25) & 1;
-    const int Wc = e.y >> 12, Wx = 2 * Wc - 1;
+    const int cu = e.x & 0x3FF, cb = (e.x >> 10) & 0x3FF, Wc = (e.x >> 20) & 0x3F;
+    const bool hx = (e.x >> 26) & 1, hy = (e.x >> 27) & 1;
     T vx = T(0), vy = T(0);
-    if (hx)
-        vx = T(0.25) * (low_res(u, b, fx, fy, px - 1, Wx) + T(2) * low_res(u, b, fx, fy, px, Wx) +
-                        low_res(u, b, fx, fy, px + 1, Wx));
-    if (hy)
-        vy = T(0.25) * (low_res(u, b, fx, fy, py - Wc, Wc) + T(2) * low_res(u, b, fx, fy, py, Wc) +
-                        low_res(u, b, fx, fy, py + Wc, Wc));
-    b[cc] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
-    u[cc] = T(0);
+    if (hx) {
+        const int pu = e.y & 0x3FF, pb = (e.y >> 10) & 0x3FF, px = e.y >> 20, py = f.x & 0x3FF, W = 2 * Wc - 1;
+        vx = T(0.25) * (low_res(u, b, fx, fy, pu - 1, pb - 1, px - 1, py - 1, W) +
+                        T(2) * low_res(u, b, fx, fy, pu, pb, px, py, W) +
+                        low_res(u, b, fx, fy, pu + 1, pb + 1, px + 1, py + 1, W));
+    }
+    if (hy) {
+        const int qu = (f.x >> 10) & 0x3FF, qb = f.x >> 20, qx = f.y & 0x3FF, qy = f.y >> 10, W = Wc;
+        vy = T(0.25) * (low_res(u, b, fx, fy, qu - W, qb - (W - 2), qx - (W - 1), qy - (W - 2), W) +
+                        T(2) * low_res(u, b, fx, fy, qu, qb, qx, qy, W) +
+                        low_res(u, b, fx, fy, qu + W, qb + (W - 2), qx + (W - 1), qy + (W - 2), W));
+    }
+    b[cb] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+    u[cu] = T(0);
 }
 
 template <class T>
-__device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint2 e, T omega)
+__host__ __device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint2 e, T omega)
 {
-    const int c = e.x & 0xFFF, W = (e.x >> 12) & 0xFF;
-    const bool iodd = (e.x >> 20) & 1, jodd = (e.x >> 21) & 1;
-    const bool hx = (e.x >> 22) & 1, hy = (e.x >> 23) & 1;
-    const int rx = e.y & 0xFFFF, ry = e.y >> 16;
+    const int c = e.x & 0x3FF, W = (e.x >> 10) & 0x3F, xf = e.x >> 20;
+    const bool iodd = (e.x >> 16) & 1, jodd = (e.x >> 17) & 1;
+    const bool hx = (e.x >> 18) & 1, hy = (e.x >> 19) & 1;
+    const int rx = e.y & 0x3FF, ry = (e.y >> 10) & 0x3FF, yf = e.y >> 20;
     T vx = T(0), vy = T(0);
     if (hx) vx = iodd ? T(0.5) * (u[rx] + u[rx + 1]) : u[rx];
     if (hy) vy = jodd ? T(0.5) * (u[ry] + u[ry + W]) : u[ry];
     T corr;
     if (hx && hy) {
-        T cxv = fx[c - 1] + fx[c], cyv = fy[c - W] + fy[c];
+        T cxv = fx[xf - 1] + fx[xf], cyv = fy[yf] + fy[yf + W - 2];
         T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
         corr = (x2 * s) * vx + (y2 * s) * vy;
     } else {
@@ -563,28 +598,39 @@ __global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su
     const SampleInfo& S = cx.samples[t.s];
     const int pi = t.seg->pi, qi = t.seg->qi;
     const LowDesc& C = descs[low_class(min(pi, dl + 1), min(qi, dl + 1), dl)];
-    const int nn = C.nn;
-    T* u = (T*)smem_raw + (size_t)slot * 4 * kLowNodes;
-    T* b = u + nn;
-    T* fx = b + nn;
-    T* fy = fx + nn;
-    for (int k = tid; k < nn; k += NT) u[k] = T(0);
+    T* u = (T*)smem_raw + (size_t)slot * kLowSlot;
+    T* b = u + C.nu;
+    T* fx = b + C.nb;
+    T* fy = fx + C.nfx;
+    for (int k = tid; k < C.nu; k += NT) u[k] = T(0);
     for (int g = 0; g < C.ngrid; ++g) {
-        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, o = w >> 8, n = low_nodes(p, q);
+        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, nx = 1 << p, W = nx + 1;
         const int64_t co = S.node_off + grid_offset(p, q, S.Q);
-        for (int k = tid; k < n; k += NT) {
-            fx[o + k] = ax[co + k];
-            fy[o + k] = ay[co + k];
+        // x-faces (i+1/2, j) of rows j = 1..ny-1, stored at node (i, j)
+        const int nxf = ((1 << q) - 1) << p;
+        for (int k = tid; k < nxf; k += NT) {
+            const int i = k & (nx - 1), j = 1 + (k >> p);
+            fx[C.gx[g] + k] = ax[co + j * W + i];
         }
-        if (p + q - 2 == dl) {
+        // y-faces (i, j+1/2) of columns i = 1..nx-1, stored at node (i, j); slot i = 0 is skipped
+        const int nyf = (1 << q) << p;
+        for (int k = tid; k < nyf; k += NT) {
+            const int i = k & (nx - 1), j = k >> p;
+            if (i == 0) continue;
+            fy[C.gy[g] + j * (nx - 1) + (i - 1)] = ay[co + j * W + i];
+        }
+        if (p + q - 2 == dl) {  // b at the interior nodes
             const int64_t so = t.scr + grid_offset(p, q, qi);
             const bool hx = p < pi, hy = q < qi;
-            for (int k = tid; k < n; k += NT) {
+            for (int k = tid; k < nxf; k += NT) {
+                const int i = k & (nx - 1), j = 1 + (k >> p);
+                if (i == 0) continue;
+                const int64_t n = so + j * W + i;
                 T v;
-                if (hx && hy) v = T(0.5) * sbx[so + k] + T(0.5) * sby[so + k];
-                else if (hy) v = sby[so + k];
-                else v = sbx[so + k];  // x-parent only, or the item's own residual
-                b[o + k] = v;
+                if (hx && hy) v = T(0.5) * sbx[n] + T(0.5) * sby[n];
+                else if (hy) v = sby[n];
+                else v = sbx[n];  // x-parent only, or the item's own residual
+                b[C.gb[g] + (j - 1) * (nx - 1) + (i - 1)] = v;
             }
         }
     }
@@ -594,7 +640,7 @@ __global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su
     const int nops = C.nops;
     for (int call = 0; call < calls; ++call) {
         // software pipeline: the words of the next two phases and this lane's
-        // first entry of the next phase are in flight while a phase runs
+        // first table word of the next phase are in flight while a phase runs
         uint2 op = nops > 0 ? rp[0] : make_uint2(0u, 0u);
         uint2 op1 = nops > 1 ? rp[1] : make_uint2(0u, 0u);
         uint2 e = low_first(ent, op, tid);
@@ -607,8 +653,9 @@ __global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su
                     low_smooth(u, b, fx, fy, e);
                     for (int k = tid + NT; k < cnt; k += NT) low_smooth(u, b, fx, fy, ent[off + k]);
                 } else if (kind == LK_RESTRICT) {
-                    low_restrict(u, b, fx, fy, e);
-                    for (int k = tid + NT; k < cnt; k += NT) low_restrict(u, b, fx, fy, ent[off + k]);
+                    low_restrict(u, b, fx, fy, e, ent[off + 2 * tid + 1]);
+                    for (int k = tid + NT; k < cnt; k += NT)
+                        low_restrict(u, b, fx, fy, ent[off + 2 * k], ent[off + 2 * k + 1]);
                 } else {
                     low_prol(u, fx, fy, e, omega);
                     for (int k = tid + NT; k < cnt; k += NT) low_prol(u, fx, fy, ent[off + k], omega);
@@ -875,18 +922,32 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
 {
     std::memset(&D, 0, sizeof(D));
     D.dl = dl;
-    int toff[kDW + 3][kDW + 3];
-    int nn = 0;
+    int gu[kDW + 3][kDW + 3], gb[kDW + 3][kDW + 3], gx[kDW + 3][kDW + 3], gy[kDW + 3][kDW + 3];
     auto exists = [&](int p, int q) { return p >= 1 && q >= 1 && p <= pic && q <= qic && p + q - 2 <= dl; };
     for (int d = 0; d <= dl; ++d)
         for (int p = 1; p <= d + 1; ++p) {
             const int q = d + 2 - p;
             if (!exists(p, q)) continue;
-            toff[p][q] = nn;
-            D.grid[D.ngrid++] = p | q << 4 | nn << 8;
-            nn += low_nodes(p, q);
+            const int nx = 1 << p, ny = 1 << q;
+            gu[p][q] = D.nu;
+            gb[p][q] = D.nb;
+            gx[p][q] = D.nfx;
+            gy[p][q] = D.nfy;
+            D.grid[D.ngrid] = p | q << 4 | D.nu << 8;
+            D.gb[D.ngrid] = D.nb;
+            D.gx[D.ngrid] = D.nfx;
+            D.gy[D.ngrid] = D.nfy;
+            ++D.ngrid;
+            D.nu += low_nodes(p, q);
+            D.nb += (nx - 1) * (ny - 1);
+            D.nfx += nx * (ny - 1);
+            D.nfy += (nx - 1) * ny;
         }
-    D.nn = nn;
+    // indices of interior node (i, j) of grid (p, q) in the four planes
+    auto U = [&](int p, int q, int i, int j) { return (uint32_t)(gu[p][q] + j * ((1 << p) + 1) + i); };
+    auto B = [&](int p, int q, int i, int j) { return (uint32_t)(gb[p][q] + (j - 1) * ((1 << p) - 1) + (i - 1)); };
+    auto X = [&](int p, int q, int i, int j) { return (uint32_t)(gx[p][q] + (j - 1) * (1 << p) + i); };
+    auto Y = [&](int p, int q, int i, int j) { return (uint32_t)(gy[p][q] + (j - 1) * ((1 << p) - 1) + (i - 1)); };
     for (int d = 0; d <= dl; ++d) {
         for (int colour = 0; colour < 2; ++colour) {  // red: (i + j) even
             D.off[d][LK_SMOOTH_RED + colour] = (int)ent.size();
@@ -897,30 +958,37 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
                 for (int j = 1; j < ny; ++j)
                     for (int i = 1; i < nx; ++i)
                         if (((i + j) & 1) == colour)
-                            ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * W + i) | (uint32_t)W << 16, 0u));
+                            ent.push_back(make_uint2(U(p, q, i, j) | B(p, q, i, j) << 10 | (uint32_t)W << 20,
+                                                     X(p, q, i, j) | Y(p, q, i, j) << 16));
             }
             D.cnt[d][LK_SMOOTH_RED + colour] = (int)ent.size() - D.off[d][LK_SMOOTH_RED + colour];
         }
         if (d == 0) continue;
-        // Eq. (2.3), one entry per interior node of each child (p, q) on diagonal
-        // d-1: R_x from the x-parent (p+1, q), R_y from the y-parent (p, q+1)
+        // Eq. (2.3), one entry (two words) per interior node (i, j) of each child
+        // (p, q) on diagonal d-1: R_x from the x-parent (p+1, q) around its node
+        // (2i, j), R_y from the y-parent (p, q+1) around its node (i, 2j)
         D.off[d][LK_RESTRICT] = (int)ent.size();
+        int nr = 0;
         for (int p = 1; p <= d; ++p) {
             const int q = d + 1 - p;
             if (!exists(p, q)) continue;
             const bool hx = exists(p + 1, q), hy = exists(p, q + 1);
             if (!hx && !hy) continue;  // only in classes no item has (pic + qic < dl + 2)
-            const int nx = 1 << p, ny = 1 << q, Wc = nx + 1, Wx = 2 * nx + 1;
+            const int nx = 1 << p, ny = 1 << q, Wc = nx + 1;
             for (int j = 1; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) {
-                    const uint32_t px = hx ? (uint32_t)(toff[p + 1][q] + j * Wx + 2 * i) : 0u;
-                    const uint32_t py = hy ? (uint32_t)(toff[p][q + 1] + 2 * j * Wc + i) : 0u;
-                    ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * Wc + i) | px << 12 | (uint32_t)hx << 24 |
-                                                 (uint32_t)hy << 25,
-                                             py | (uint32_t)Wc << 12));
+                    const uint32_t pu = hx ? U(p + 1, q, 2 * i, j) : 0u, pb = hx ? B(p + 1, q, 2 * i, j) : 0u;
+                    const uint32_t px = hx ? X(p + 1, q, 2 * i, j) : 0u, py = hx ? Y(p + 1, q, 2 * i, j) : 0u;
+                    const uint32_t qu = hy ? U(p, q + 1, i, 2 * j) : 0u, qb = hy ? B(p, q + 1, i, 2 * j) : 0u;
+                    const uint32_t qx = hy ? X(p, q + 1, i, 2 * j) : 0u, qy = hy ? Y(p, q + 1, i, 2 * j) : 0u;
+                    ent.push_back(make_uint2(U(p, q, i, j) | B(p, q, i, j) << 10 | (uint32_t)Wc << 20 |
+                                                 (uint32_t)hx << 26 | (uint32_t)hy << 27,
+                                             pu | pb << 10 | px << 20));
+                    ent.push_back(make_uint2(py | qu << 10 | qb << 20, qx | qy << 10));
+                    ++nr;
                 }
         }
-        D.cnt[d][LK_RESTRICT] = (int)ent.size() - D.off[d][LK_RESTRICT];
+        D.cnt[d][LK_RESTRICT] = nr;
         // Eq. (2.4)/(2.5): linear prolongation from each child, kappa-weighted
         D.off[d][LK_PROL] = (int)ent.size();
         for (int p = 1; p <= d + 1; ++p) {
@@ -930,12 +998,12 @@ static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<ui
             const bool hx = p > 1, hy = q > 1;
             for (int j = 1; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) {
-                    const uint32_t rx = hx ? (uint32_t)(toff[p - 1][q] + j * Wc + (i >> 1)) : 0u;
-                    const uint32_t ry = hy ? (uint32_t)(toff[p][q - 1] + (j >> 1) * W + i) : 0u;
-                    ent.push_back(make_uint2((uint32_t)(toff[p][q] + j * W + i) | (uint32_t)W << 12 |
-                                                 (uint32_t)(i & 1) << 20 | (uint32_t)(j & 1) << 21 |
-                                                 (uint32_t)hx << 22 | (uint32_t)hy << 23,
-                                             rx | ry << 16));
+                    const uint32_t rx = hx ? (uint32_t)(gu[p - 1][q] + j * Wc + (i >> 1)) : 0u;
+                    const uint32_t ry = hy ? (uint32_t)(gu[p][q - 1] + (j >> 1) * W + i) : 0u;
+                    ent.push_back(make_uint2(U(p, q, i, j) | (uint32_t)W << 10 | (uint32_t)(i & 1) << 16 |
+                                                 (uint32_t)(j & 1) << 17 | (uint32_t)hx << 18 | (uint32_t)hy << 19 |
+                                                 X(p, q, i, j) << 20,
+                                             rx | ry << 10 | Y(p, q, i, j) << 20));
                 }
         }
         D.cnt[d][LK_PROL] = (int)ent.size() - D.off[d][LK_PROL];
@@ -1486,13 +1554,13 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             if (C.low_threads == 32) {  // one warp per item, low_warps items per CTA
                 const int lw = C.low_warps;
                 const unsigned nb = (unsigned)((nitems + lw - 1) / lw);
-                k_low<T, 32><<<nb, lw * 32, sizeof(T) * 4 * kLowNodes * lw, st>>>(
+                k_low<T, 32><<<nb, lw * 32, sizeof(T) * kLowSlot * lw, st>>>(
                     ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             } else if (C.low_threads == 64) {  // one item per CTA
-                k_low<T, 64><<<(unsigned)nitems, 64, sizeof(T) * 4 * kLowNodes, st>>>(
+                k_low<T, 64><<<(unsigned)nitems, 64, sizeof(T) * kLowSlot, st>>>(
                     ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             } else {
-                k_low<T, 128><<<(unsigned)nitems, 128, sizeof(T) * 4 * kLowNodes, st>>>(
+                k_low<T, 128><<<(unsigned)nitems, 128, sizeof(T) * kLowSlot, st>>>(
                     ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
             }
             prof_end(K_LOW, st, low_bytes, 0.0, d);
@@ -1608,7 +1676,7 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-    if (sizeof(T) * 4 * kLowNodes * C.low_warps > kSmemMax) {
+    if (sizeof(T) * kLowSlot * C.low_warps > kSmemMax) {
         set_error("tune_low_warps items do not fit the shared memory of one CTA");
         return MSG_ERR_INVALID;
     }
@@ -1630,11 +1698,11 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * std::max(kBandNodes, 3 * ((1 << 12) + 1)))));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes * C.low_warps)));
+                                      (int)(sizeof(T) * kLowSlot * C.low_warps)));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes)));
+                                      (int)(sizeof(T) * kLowSlot)));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * 4 * kLowNodes)));
+                                      (int)(sizeof(T) * kLowSlot)));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- one worker (host thread + stream) per stage
