@@ -151,9 +151,10 @@ def oracle_throughput(a, n_samples=None, threads=None, seed=1):
     Zs = [oracle.kl_field(Phi, sl, oracle.normals(seed, 10**6 + i, a.M)) for i in range(n)]
     prm = oracle.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega)
     t0 = time.time()
-    oracle.solve_batch([(a.P, a.Q)] * n, Zs, prm, threads=threads)
+    used = min(threads, n)  # one sample per thread: threads beyond n stay idle
+    oracle.solve_batch([(a.P, a.Q)] * n, Zs, prm, threads=used)
     wall = time.time() - t0
-    return n / wall, threads, n, wall
+    return n / wall, used, n, wall
 
 
 def reference_arm(a, rank, world):
