@@ -176,8 +176,9 @@ def test_constant_coefficient_fmsg_matches_sine_solution():
                                                  (3, 3, 0.0334230, None), (3, 6, 0.0342545, None),
                                                  (6, 6, 0.0351164, 0.0736572)])
 def test_constant_coefficient_printed_values(p, q, integral, center):
-    """Integral and midpoint values of the a = 1 discrete solutions (sine-series
-    values tabulated in the survey of this build; 1/64 and 1/16 on G^(1,1) by hand)."""
+    """Integral and midpoint values of the a = 1 discrete solutions: the discrete
+    sine-series (DST) closed form summed to 7 digits, and 1/64 and 1/16 on G^(1,1)
+    by hand (one unknown, A = 8 + 8 = 16, u = 1/16, integral = u / 4)."""
     Qg, st, _, _ = oracle.solve_sample(p, q, np.zeros(oracle.field_points(p, q)),
                                        oracle.SolverParams(eps=1e-12, max_cycles=100))
     assert Qg[p - 1, q - 1] == pytest.approx(integral, abs=6e-8)
