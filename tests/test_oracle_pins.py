@@ -1,8 +1,8 @@
 """Pins of the CPU oracle against facts that do not come from the oracle itself.
 
-Each test names what fixes the expected value: a closed form, a published
-known-answer vector, an independent library implementation, an invariant of
-the method, or a value printed in arXiv:1907.12334.  Chosen so that a dropped
+Each test names what fixes the expected value: a closed form, an independent
+library implementation, an invariant of the method, or a value printed in
+arXiv:1907.12334.  Chosen so that a dropped
 term, a wrong sign or index, or a transposed operand in the oracle fails at
 least one of them.
 """
@@ -20,16 +20,7 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 # --------------------------------------------------------------- generator --
 
-def test_philox_known_answer_vector():
-    """Random123 known-answer vector for Philox4x64-10 (Salmon et al., SC'11)."""
-    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x64_10_kat.txt")) if l.strip() and l[0] != "#"]
-    for r in rows:
-        v = [int(x, 16) for x in r]
-        out = oracle.philox4x64_10(v[0:4], v[4:6])
-        assert [int(x) for x in out] == v[6:10]
-
-
-@pytest.mark.parametrize("ctr,key", [((5, 7, 0, 0), (123, 0)), ((0, 3, 0, 0), (2**63 + 11, 0)),
+@pytest.mark.parametrize("ctr,key", [((0, 0, 0, 0), (0, 0)), ((5, 7, 0, 0), (123, 0)), ((0, 3, 0, 0), (2**63 + 11, 0)),
                                      ((2**40, 2**33, 9, 2**62), (1, 2**64 - 1))])
 def test_philox_matches_numpy(ctr, key):
     """numpy.random.Philox is an independent Philox4x64-10; it pre-increments its counter."""
