@@ -168,7 +168,8 @@ int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int32_t q0, co
 /* device; make that call before any stream capture.  All calls share the     */
 /* array and return after their work has finished on `stream`; calls that     */
 /* overlap on the GPU race.  The array holds no state a call needs: each call  */
-/* writes the whole table it reads.                                           */
+/* writes the whole table it reads.  The cached address does not survive a    */
+/* cudaDeviceReset of that device in the same process.                        */
 int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t p0, int32_t q0, const double* Q,
                                  const double* ptau, int32_t ld1, int32_t ld2, double* dQ, double* Y, void* stream);
 

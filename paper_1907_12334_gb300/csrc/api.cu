@@ -83,7 +83,6 @@ void prof_end(int cls, cudaStream_t st, double bytes, double flops, int level)
     g_prof.recs.push_back(Rec{t_pending_start[cls], e, cls, level, bytes, flops});
 }
 
-void prof_count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace msg
 

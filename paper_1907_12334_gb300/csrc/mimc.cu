@@ -104,7 +104,9 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
 // symbol: every GPU that loads the library holds it until the process exits.
 // In host code its name is only a host-side stand-in, so the device address
 // is looked up with cudaGetSymbolAddress once per device (on the first call
-// made with that device current) and cached.
+// made with that device current) and cached.  The cache is not invalidated by
+// cudaDeviceReset: after a reset of a device in this process the entry point
+// must not be called on that device again.
 // ---------------------------------------------------------------------------
 namespace msg {
 namespace {
@@ -157,11 +159,16 @@ extern "C" int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t
     const size_t tb = sizeof(MimcSample) * (size_t)S;
     const size_t tb_al = (tb + 255) / 256 * 256;
     const size_t pb = ptau ? sizeof(double) * (size_t)std::max(ld1, 0) * (size_t)std::max(ld2, 0) : 0;
+    if (pb >= kNoAllocBytes) {
+        set_error("mimc_differences_noalloc: the ptau table alone (" + std::to_string(pb) +
+                  " bytes) does not fit the fixed " + std::to_string(kNoAllocBytes) + "-byte scratch");
+        return MSG_ERR_INVALID;
+    }
     if (tb_al + pb > kNoAllocBytes) {
         set_error("mimc_differences_noalloc: batch needs " + std::to_string(tb_al + pb) +
                   " bytes of scratch, more than the fixed " + std::to_string(kNoAllocBytes) +
-                  " (at most about " + std::to_string((kNoAllocBytes - pb) / sizeof(MimcSample)) +
-                  " samples per call)");
+                  " (with this ptau table at most " +
+                  std::to_string((kNoAllocBytes - pb) / 256 * 256 / sizeof(MimcSample)) + " samples per call)");
         return MSG_ERR_INVALID;
     }
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -193,8 +200,9 @@ extern "C" int32_t mimc_differences_noalloc(const int32_t* L, int64_t S, int32_t
     MSG_CUDA_TRY(cudaMemcpyAsync(d, g_noalloc_host, tb_al + pb, cudaMemcpyHostToDevice, st));
     const double* dp = ptau ? (const double*)(d + tb_al) : nullptr;
     int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
+    prof_begin(K_MIMC, st);
     k_mimc<<<blocks, 256, 0, st>>>((const MimcSample*)d, S, p0, q0, Q, dp, ld2, dQ, Y);
-    prof_count();
+    prof_end(K_MIMC, st, 8.0 * (qo + 2.0 * dof) + tb, 0.0);
     MSG_CHECK_LAUNCH();
     // the host staging and the device array are reused by the next call
     MSG_CUDA_TRY(cudaStreamSynchronize(st));

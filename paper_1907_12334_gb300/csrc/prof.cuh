@@ -27,7 +27,5 @@ enum KernelClass {
 // launches with their diagonal (-1: none).
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double bytes, double flops, int level = -1);
-// count one launch without recording events
-void prof_count();
 
 }  // namespace msg

@@ -25,7 +25,8 @@ MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32 = 0, 1, 2
 MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
-            "msg_solve_batch", "mimc_differences", "msg_last_error", "msg_version", "msg_launch_count",
+            "msg_solve_batch", "mimc_differences", "mimc_differences_noalloc", "msg_last_error", "msg_version",
+            "msg_launch_count",
             "msg_profile_enable", "msg_profile_read", "msg_profile_read_level")
 KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
 

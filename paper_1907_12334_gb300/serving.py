@@ -62,6 +62,7 @@ class MimcDriver:
         self.sdq = np.zeros((n1, n2))
         self.sdq2 = np.zeros((n1, n2))
         self.cnt = np.zeros((n1, n2))
+        self.skipped: dict[str, np.ndarray] = {}  # reason -> per-index count of samples without a Y
         self.cost = np.array([[2.0 ** ((self.p0 + a) + (self.q0 + b)) for b in range(n2)] for a in range(n1)])
 
     def pmf(self):
@@ -93,6 +94,30 @@ class MimcDriver:
         if self.n % self.learn_every == 0:
             self.learn()
         return Y
+
+    def take(self, req):
+        """Fold one finished request into the estimator (record) or the skip counts."""
+        if req.status == 0 and req.dQ is not None:
+            return self.record(req.L, req.dQ, req.ptau)
+        self.skip(req.L, req.status)
+        return None
+
+    def skip(self, L, status):
+        """Count a sample that gives no Y: its solve did not converge or became
+        non-finite, its batch failed, or it was refused.  Leaving such samples out
+        reweights Eq. (3.6) towards the indices that converge, so the counts are
+        reported beside E and V (``skipped_report``)."""
+        if status < 0:
+            key = "refused" if status == -1 else "batch_failed"
+        elif status & 2:
+            key = "nonfinite"
+        else:
+            key = "not_converged"
+        self.skipped.setdefault(key, np.zeros_like(self.cnt))[L[0], L[1]] += 1
+
+    def skipped_report(self):
+        """{reason: {(l1, l2): count}} of the samples left out of E and V."""
+        return {k: {(int(a), int(b)): int(v[a, b]) for a, b in zip(*np.nonzero(v))} for k, v in self.skipped.items()}
 
     def learn(self):
         """Tail probabilities proportional to sqrt(V_l / C_l), normalised to p_0 = 1 and made
@@ -130,6 +155,9 @@ class MimcDriver:
 
 # ------------------------------------------------------------------ server --
 
+STATUS_REFUSED = -1       # request larger than the whole HBM budget
+STATUS_BATCH_FAILED = -2  # the batch's library call raised; Q and dQ are None
+
 @dataclass
 class Request:
     rid: int
@@ -141,7 +169,8 @@ class Request:
     t_done: float = 0.0
     Q: np.ndarray | None = None
     dQ: np.ndarray | None = None
-    status: int = 0
+    status: int = 0  # MSG_SAMPLE_* bits of the solve, or STATUS_REFUSED / STATUS_BATCH_FAILED
+    error: str = ""
 
 
 class Server:
@@ -168,6 +197,7 @@ class Server:
         self.in_use = 0
         self.done: list[Request] = []
         self.rejected = 0
+        self.failures: list[str] = []
         self.slots = slots
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
         self.busy = [False] * slots
@@ -237,6 +267,14 @@ class Server:
                 od += a * b
                 r.status = int(sth[k])
                 r.t_done = t
+        except Exception as exc:  # a library or allocation failure fails the whole batch, visibly
+            t = time.perf_counter()
+            for r in reqs:
+                r.status = STATUS_BATCH_FAILED
+                r.Q = r.dQ = None
+                r.error = repr(exc)
+                r.t_done = t
+            self.failures.append(repr(exc))
         finally:
             with self.cv:
                 self.in_use -= self.request_bytes([r.shape for r in reqs])
@@ -281,7 +319,7 @@ class Server:
                         if not batch and self.in_use == 0:
                             self.rejected += 1  # a single request above the budget: refused
                             pending.remove(r)
-                            r.status = -1
+                            r.status = STATUS_REFUSED
                             r.t_done = time.perf_counter()
                             self.done.append(r)
                         break
@@ -321,7 +359,8 @@ class Server:
 
 def run_driver(server: Server, driver: MimcDriver, rate_hz: float, max_samples: int, seed: int = 1):
     """Feed the server with Poisson arrivals of driver requests until sqrt(V) <= eps
-    (or max_samples); returns (driver, results, wall seconds)."""
+    (or max_samples); returns (driver, results, wall seconds).  Samples without a
+    usable result are counted per multi-index in ``driver.skipped_report()``."""
     rng = np.random.default_rng(seed)
     results = []
     sent = 0
@@ -347,8 +386,7 @@ def run_driver(server: Server, driver: MimcDriver, rate_hz: float, max_samples: 
             fresh = server.done[seen:]
             seen = len(server.done)
         for r in fresh:
-            if r.status == 0:
-                driver.record(r.L, r.dQ, r.ptau)
+            driver.take(r)
             results.append(r)
         if feeder_done.is_set() and seen >= sent:
             break

@@ -34,6 +34,10 @@ MUTATIONS = [
     ("mixed difference term", "if (t1 > 0) d1_at_t2m1 -= Qgrid[(p0 + t1 - 2) * Qn + (q0 + t2 - 2)];",
      "", "worked_example or telescoping"),
     ("philox multiplier", "0xD2E7470EE14C6C93ULL * x0", "0xD2E7470EE14C6C95ULL * x0", "philox"),
+    ("flux boundary column", "double a = exp(Z[(int64_t)(2 * j * sy) * NFx + (NFx - 1)]);",
+     "double a = exp(Z[(int64_t)(2 * j * sy) * NFx + (NFx - 2)]);", "boundary_column"),
+    ("flux boundary row", "double a = exp(Z[(int64_t)(2 * j * sy) * NFx + (NFx - 1)]);",
+     "double a = exp(Z[(int64_t)(2 * j * sy + 1) * NFx + (NFx - 1)]);", "boundary_column"),
     ("box-muller radius", "double rad = sqrt(-2.0 * log(1.0 - ua));", "double rad = sqrt(-1.0 * log(1.0 - ua));",
      "normals_distribution"),
 ]

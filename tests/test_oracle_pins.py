@@ -397,6 +397,28 @@ def test_qoi_closed_forms():
     assert H.qoi(P, Q, qoi=oracle.QOI_SUBDOMAIN) == pytest.approx(0.375, rel=1e-14)
 
 
+def test_flux_qoi_reads_the_boundary_column_of_a_varying_field():
+    """Q3 of Sec. 4 takes a(1, y_j) from the field's boundary column x = 1.  With
+    Z(x, y) = 3x + log(1 + y) on the field nodes, a(1, y) = e^3 (1 + y), and the nodal
+    v = x(1-x) y(1-y) on grid (p,q) gives v_{nx-1,j}/dx = (1 - dx) y_j (1 - y_j), so
+    Q3 = e^3 (1 - dx) dy sum_j (y_j - y_j^3) = e^3 (1 - dx) [(1 - dy)/2 - (1 - dy)^2/4]
+    (sum_j j = n(n-1)/2, sum_j j^3 = (n(n-1)/2)^2).  A column one node inside (a(1-h, y))
+    or a row shifted by one field node changes the value; grids coarser than the
+    field's finest (sy > 1) check the row stride."""
+    P, Q = 3, 4
+    NFx, NFy = (1 << (P + 1)) + 1, (1 << (Q + 1)) + 1
+    FX, FY = np.meshgrid(np.arange(NFx) / (NFx - 1), np.arange(NFy) / (NFy - 1))
+    Z = 3.0 * FX + np.log1p(FY)
+    H = oracle.Hierarchy(P, Q, Z=Z.ravel())
+    for p, q in [(P, Q), (2, 3), (3, 1), (1, 2)]:
+        nx, ny = 1 << p, 1 << q
+        X, Y = np.meshgrid(np.arange(nx + 1) / nx, np.arange(ny + 1) / ny)
+        H.set(p, q, oracle.SOL, X * (1 - X) * Y * (1 - Y))
+        dx, dy = 1 / nx, 1 / ny
+        want = np.exp(3.0) * (1 - dx) * ((1 - dy) / 2 - (1 - dy) ** 2 / 4)
+        assert H.qoi(p, q, qoi=oracle.QOI_FLUX) == pytest.approx(want, rel=1e-13), (p, q)
+
+
 # ------------------------------------------------------------------- MIMC --
 
 def test_mixed_difference_worked_example():

@@ -97,3 +97,45 @@ def test_admission_respects_the_hbm_budget():
     srv2 = Server(hbm_budget_bytes=int(2.5 * small), max_batch=8, slots=3, M=16, prm=prm)
     out2 = srv2.serve([Request(rid=i, sample=i, L=(0, 0), shape=(2, 2), ptau=np.ones((1, 1))) for i in range(6)])
     assert len(out2) == 6 and all(r.status == 0 for r in out2) and srv2.rejected == 0
+
+
+def test_failed_batch_is_marked_and_skipped_by_the_driver():
+    """A library error inside a batch marks every request of that batch as failed
+    (status -2, no Q/dQ); the driver leaves them out of E and V and counts them per
+    multi-index instead of crashing on the missing differences."""
+    import contextlib
+    import types
+
+    from paper_1907_12334_gb300 import serving
+    from paper_1907_12334_gb300.serving import Request, Server
+
+    class Boom(RuntimeError):
+        pass
+
+    def fail(*a, **k):
+        raise Boom("libmsgmimc error 3: simulated failure")
+
+    fake_msg = types.SimpleNamespace(packed_sizes=fail, field_points=lambda P, Q: 1,
+                                     msg_workspace_bytes=lambda pq, prm: 0)
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(stream=lambda st: contextlib.nullcontext()))
+    srv = Server.__new__(Server)
+    srv.torch, srv.msg, srv.prm, srv.M = fake_torch, fake_msg, None, 8
+    srv.streams, srv.busy, srv.done, srv.failures = [None], [True], [], []
+    srv.cv, srv.in_use, srv.batches = serving.threading.Condition(), 0, 0
+    drv = MimcDriver(eps=1e-3, lmax=(2, 2))
+    reqs = [Request(rid=i, sample=i, L=(i % 2, 1), shape=drv.shape((i % 2, 1)), ptau=drv.tail) for i in range(3)]
+    srv._run_batch(0, reqs)
+    assert [r.status for r in srv.done] == [serving.STATUS_BATCH_FAILED] * 3
+    assert all(r.Q is None and r.dQ is None and "simulated" in r.error for r in srv.done)
+    assert len(srv.failures) == 1 and srv.busy == [False]
+    ok = Request(rid=9, sample=9, L=(0, 0), shape=drv.shape((0, 0)), ptau=drv.tail, dQ=np.ones((1, 1)))
+    for r in srv.done + [ok]:
+        drv.take(r)
+    assert drv.n == 1 and drv.E == 1.0
+    assert drv.skipped_report() == {"batch_failed": {(0, 1): 2, (1, 1): 1}}
+    nc = Request(rid=10, sample=10, L=(2, 2), shape=drv.shape((2, 2)), ptau=drv.tail, status=1)
+    nf = Request(rid=11, sample=11, L=(2, 0), shape=drv.shape((2, 0)), ptau=drv.tail, status=3)
+    drv.take(nc)
+    drv.take(nf)
+    rep = drv.skipped_report()
+    assert rep["not_converged"] == {(2, 2): 1} and rep["nonfinite"] == {(2, 0): 1}

@@ -67,3 +67,49 @@ def test_noalloc_rejects_batches_beyond_its_fixed_scratch(msg):
             ctypes.c_void_p(dummy.data_ptr()), None, None)
     assert rc == msg.MSG_ERR_INVALID
     assert b"fixed" in lib.msg_last_error()
+
+
+def _raw(msg):
+    lib = msg.load()
+    fn = lib.mimc_differences_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int32
+    return lib, fn
+
+
+def test_noalloc_fills_its_scratch_exactly_and_rejects_one_row_more(msg):
+    """The limit is the table (24 bytes per sample, rounded up to 256) plus the
+    ptau table: a batch that fills the 16 MiB array exactly runs and matches
+    mimc_differences; the same batch with one more ptau row is refused, and a
+    ptau table larger than the whole array is refused with its own message."""
+    S = 699_040  # 24 S = 16 776 960 bytes = 65 535 x 256, leaving 256 bytes = a 4 x 8 ptau table
+    rng = np.random.default_rng(3)
+    Ls = np.zeros((S, 2), dtype=np.int32)
+    Ls[::97] = (3, 7)
+    Ls[5::89] = (1, 2)
+    p0 = q0 = 1
+    nq = int(((p0 + Ls[:, 0]) * (q0 + Ls[:, 1])).sum())
+    nd = int(((Ls[:, 0] + 1) * (Ls[:, 1] + 1)).sum())
+    Q = torch.from_numpy(rng.standard_normal(nq)).cuda()
+    ptau = np.exp(-1.3 * (np.arange(4)[:, None] + np.arange(8)[None, :]))
+    out = {}
+    for name, fn in (("alloc", msg.mimc_differences), ("noalloc", msg.mimc_differences_noalloc)):
+        dQ = torch.full((nd,), np.nan, dtype=torch.float64, device="cuda")
+        Y = torch.full((S,), np.nan, dtype=torch.float64, device="cuda")
+        fn(Ls, p0, q0, Q, dQ, ptau=ptau, Y=Y)
+        torch.cuda.synchronize()
+        out[name] = (dQ.cpu().numpy(), Y.cpu().numpy())
+    assert np.array_equal(out["noalloc"][0], out["alloc"][0])
+    assert np.array_equal(out["noalloc"][1], out["alloc"][1])
+    lib, fn = _raw(msg)
+    dummy = torch.empty(1, dtype=torch.float64, device="cuda")
+    dp = ctypes.c_void_p(dummy.data_ptr())
+    big = np.exp(-1.3 * (np.arange(5)[:, None] + np.arange(8)[None, :]))
+    rc = fn(Ls.ctypes.data_as(ctypes.c_void_p), S, p0, q0, dp, big.ctypes.data_as(ctypes.c_void_p), 5, 8, dp, dp,
+            None)
+    assert rc == msg.MSG_ERR_INVALID and b"fixed" in lib.msg_last_error()
+    huge = np.ones((1500, 1500))
+    rc = fn(Ls.ctypes.data_as(ctypes.c_void_p), 1, p0, q0, dp, huge.ctypes.data_as(ctypes.c_void_p), 1500, 1500, dp,
+            dp, None)
+    assert rc == msg.MSG_ERR_INVALID and b"ptau table alone" in lib.msg_last_error()
