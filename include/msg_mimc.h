@@ -141,6 +141,19 @@ int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, con
                         int32_t* status, int32_t* cycles, double* relres, void* workspace, size_t ws_bytes,
                         void* stream);
 
+/* Solutions on every grid (Algorithm 2 returns one per grid of the hierarchy). */
+/* After msg_solve_batch has run on `workspace` (same PQ, S, prm; stream-      */
+/* ordered after it), msg_solution copies the FP64 solution u of every grid of */
+/* every sample into u_out: sample i's block of msg_solution_values(PQ+2i, 1)  */
+/* values follows sample i-1's; inside it grid (p,q) starts at                 */
+/* T(p-1) T(Q_i) + (2^p+1) T(q-1), T(n) = 2^(n+1) - 2 + n, and holds its       */
+/* (2^p+1)(2^q+1) nodes row by row (x fastest), boundary zeros included.       */
+/*   u_out [device] double [msg_solution_values(PQ, S)], written.              */
+/* msg_solution_values returns the count (host only; -1 on a bad shape).       */
+int64_t msg_solution_values(const int32_t* PQ, int64_t S);
+int32_t msg_solution(const int32_t* PQ, int64_t S, const msg_params* prm, const void* workspace, size_t ws_bytes,
+                     double* u_out, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (a14) Multi-index differences (Sec. 3, Eq. (3.2)) and Y (Eq. (3.6)).       */
 /*                                                                          */

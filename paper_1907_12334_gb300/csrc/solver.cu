@@ -1787,3 +1787,39 @@ extern "C" int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_param
     if (prm->precision == MSG_PREC_MIXED) return run_solve<float>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
     return run_solve<double>(pl, wl, ws, *prm, Z, Qout, stat, cycles, relres, st);
 }
+
+extern "C" int32_t msg_solution(const int32_t* PQ, int64_t S, const msg_params* prm, const void* workspace,
+                                size_t ws_bytes, double* u_out, void* stream)
+{
+    clear_error();
+    int rc = validate(PQ, S, prm);
+    if (rc != MSG_OK) return rc;
+    if (S == 0) return MSG_OK;
+    if (!workspace || !u_out) { set_error("workspace and u_out must be non-NULL"); return MSG_ERR_INVALID; }
+    Plan pl;
+    build_plan(PQ, S, pl);
+    WsLayout wl = layout_of(pl, *prm);
+    if (ws_bytes < wl.total + align_up(sizeof(int32_t) * S)) {
+        set_error("workspace smaller than msg_workspace_bytes for this batch");
+        return MSG_ERR_WORKSPACE;
+    }
+    const char* ws = (const char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    MSG_CUDA_TRY(cudaMemcpyAsync(u_out, ws + wl.u64, sizeof(double) * pl.total_nodes, cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream));
+    return MSG_OK;
+}
+
+extern "C" int64_t msg_solution_values(const int32_t* PQ, int64_t S)
+{
+    clear_error();
+    if (S < 0 || (S > 0 && !PQ)) { set_error("bad PQ / S"); return -1; }
+    int64_t n = 0;
+    for (int64_t i = 0; i < S; ++i) {
+        if (PQ[2 * i] < 1 || PQ[2 * i] > 12 || PQ[2 * i + 1] < 1 || PQ[2 * i + 1] > 12) {
+            set_error("grid exponents must satisfy 1 <= P, Q <= 12");
+            return -1;
+        }
+        n += rect_nodes(PQ[2 * i], PQ[2 * i + 1]);
+    }
+    return n;
+}

@@ -25,7 +25,8 @@ MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32 = 0, 1, 2
 MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
-            "msg_solve_batch", "mimc_differences", "mimc_differences_noalloc", "msg_last_error", "msg_version",
+            "msg_solve_batch", "msg_solution_values", "msg_solution", "mimc_differences",
+            "mimc_differences_noalloc", "msg_last_error", "msg_version",
             "msg_launch_count",
             "msg_profile_enable", "msg_profile_read", "msg_profile_read_level")
 KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
@@ -95,6 +96,10 @@ def load(path: str | None = None):
     L.msg_workspace_bytes.restype = sz
     L.msg_solve_batch.argtypes = [vp, i64, ctypes.POINTER(msg_params), vp, vp, vp, vp, vp, vp, sz, vp]
     L.msg_solve_batch.restype = i32
+    L.msg_solution_values.argtypes = [vp, i64]
+    L.msg_solution_values.restype = i64
+    L.msg_solution.argtypes = [vp, i64, ctypes.POINTER(msg_params), vp, sz, vp, vp]
+    L.msg_solution.restype = i32
     L.mimc_differences.argtypes = [vp, i64, i32, i32, vp, vp, i32, i32, vp, vp, vp]
     L.mimc_differences.restype = i32
     L.msg_last_error.argtypes = []
@@ -180,6 +185,29 @@ def msg_solve_batch(PQ, prm: SolverParams, Z, Qout, status=None, cycles=None, re
                                   workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
+def msg_solution_values(PQ) -> int:
+    pq = _host_i32(PQ).reshape(-1, 2)
+    n = int(load().msg_solution_values(pq.ctypes.data_as(ctypes.c_void_p), pq.shape[0]))
+    if n < 0:
+        raise MsgError(load().msg_last_error().decode())
+    return n
+
+
+def msg_solution(PQ, prm: SolverParams, workspace, u_out, stream=None):
+    """FP64 solutions of every grid, from a workspace msg_solve_batch has just filled."""
+    pq = _host_i32(PQ).reshape(-1, 2)
+    c = prm.c()
+    _check(load().msg_solution(pq.ctypes.data_as(ctypes.c_void_p), pq.shape[0], ctypes.byref(c), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _ptr(u_out), _stream(stream)))
+
+
+def grid_view(u_block, P: int, Q: int, p: int, q: int):
+    """Grid (p,q) of one sample's solution block (see msg_solution) as a [2^q+1, 2^p+1] array view."""
+    T = lambda n: (2 << n) - 2 + n
+    o = T(p - 1) * T(Q) + ((1 << p) + 1) * T(q - 1)
+    return u_block[o:o + ((1 << p) + 1) * ((1 << q) + 1)].reshape((1 << q) + 1, (1 << p) + 1)
+
+
 def mimc_differences(L, p0: int, q0: int, Q, dQ, ptau=None, Y=None, stream=None):
     Lh = _host_i32(L).reshape(-1, 2)
     if ptau is not None:
@@ -234,10 +262,11 @@ def packed_sizes(PQ):
     return nq, nf
 
 
-def solve(PQ, Z, prm: SolverParams | None = None, stream=None):
+def solve(PQ, Z, prm: SolverParams | None = None, stream=None, with_u: bool = False):
     """Allocate outputs + workspace with torch and run msg_solve_batch.
 
-    Returns (Q, status, cycles, relres) as device tensors (Q/cycles/relres packed per sample)."""
+    Returns (Q, status, cycles, relres) as device tensors (Q/cycles/relres packed per sample),
+    and the FP64 solutions of every grid (msg_solution layout) as a fifth item if with_u."""
     import torch
 
     prm = prm or SolverParams()
@@ -251,6 +280,10 @@ def solve(PQ, Z, prm: SolverParams | None = None, stream=None):
     relres = torch.empty(nq, dtype=torch.float64, device=dev)
     ws = torch.empty(msg_workspace_bytes(pq, prm), dtype=torch.uint8, device=dev)
     msg_solve_batch(pq, prm, Z, Q, status, cycles, relres, ws, stream)
+    if with_u:
+        u = torch.empty(msg_solution_values(pq), dtype=torch.float64, device=dev)
+        msg_solution(pq, prm, ws, u, stream)
+        return Q, status, cycles, relres, u
     return Q, status, cycles, relres
 
 

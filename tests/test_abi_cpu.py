@@ -117,3 +117,22 @@ def test_profiling_api_host_logic(lib):
     assert lib.msg_profile_read(99, ctypes.byref(n), ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == \
         msg.MSG_ERR_INVALID
     msg.msg_profile_enable(False)
+
+
+def test_solution_values_count_and_grid_offsets(lib):
+    """msg_solution_values = sum over samples of T(P) T(Q) nodes, T(n) = 2^(n+1) - 2 + n; grid_view
+    places grid (p,q) at T(p-1) T(Q) + (2^p+1) T(q-1) and the last grid ends the block."""
+    T = lambda n: (2 << n) - 2 + n
+    shapes = [(3, 5), (1, 1), (8, 2)]
+    assert msg.msg_solution_values(shapes) == sum(T(P) * T(Q) for P, Q in shapes)
+    P, Q = 4, 3
+    blk = np.arange(T(P) * T(Q), dtype=np.float64)
+    seen = np.zeros(blk.size, dtype=int)
+    for p in range(1, P + 1):
+        for q in range(1, Q + 1):
+            g = msg.grid_view(blk, P, Q, p, q)
+            assert g.shape == ((1 << q) + 1, (1 << p) + 1)
+            seen[g.ravel().astype(int)] += 1
+    assert (seen == 1).all()  # the grids tile the block exactly
+    with pytest.raises(msg.MsgError):
+        msg.msg_solution_values([(0, 3)])
