@@ -139,3 +139,39 @@ def test_failed_batch_is_marked_and_skipped_by_the_driver():
     drv.take(nf)
     rep = drv.skipped_report()
     assert rep["not_converged"] == {(2, 2): 1} and rep["nonfinite"] == {(2, 0): 1}
+
+
+@pytest.mark.gpu
+def test_served_results_match_the_oracle():
+    """Requests served through continuous batching (several concurrent batches,
+    uneven shapes) against the oracle solving the same fields: each grid's Q to the
+    mixed path's relative 1e-8, and dQ to 1e-8 max|Q| (differences tend to zero, so
+    they are compared absolutely at the scale of Q)."""
+    pytest.importorskip("torch")
+    import oracle
+    from paper_1907_12334_gb300 import inputs, msg
+    from paper_1907_12334_gb300.serving import Request, Server
+
+    M, seed = 24, 4
+    prm = msg.SolverParams(eps=1e-10, max_cycles=400)
+    drv = MimcDriver(eps=1e-3, lmax=(3, 3), seed=11)
+    Ls = drv.draw(18)
+    reqs = [Request(rid=i, sample=100 + i, L=L, shape=drv.shape(L), ptau=drv.tail) for i, L in enumerate(Ls)]
+    srv = Server(hbm_budget_bytes=2 << 30, max_batch=5, slots=3, M=M, seed=seed, prm=prm)
+    done = {r.rid: r for r in srv.serve(reqs)}
+    assert len(done) == len(reqs) and not srv.failures
+    checked = 0
+    for r in reqs:
+        got = done[r.rid]
+        if got.status != 0:
+            continue
+        P, Qn = r.shape
+        Phi, sl = inputs.kl_basis(P, Qn, inputs.FieldLaw(M=M))
+        Z = oracle.kl_field(Phi, sl, oracle.normals(seed, r.sample, M))
+        Qo, st, _, _ = oracle.solve_sample(P, Qn, Z, oracle.SolverParams(eps=1e-12, max_cycles=600))
+        assert st == 0
+        np.testing.assert_allclose(got.Q, Qo, rtol=1e-8)
+        dQo, _ = oracle.mimc_differences(r.L, srv.p0, srv.q0, Qo)
+        np.testing.assert_allclose(got.dQ, dQo, rtol=0, atol=1e-8 * np.abs(Qo).max())
+        checked += 1
+    assert checked >= 0.9 * len(reqs)
