@@ -12,11 +12,11 @@
 // For a linear cycle this is the same iteration as cycling on (u, 1).
 //
 // Launch structure of one cycle for all active items of a stage: diagonals
-// d > kDW of the items' hierarchies are visited by one launch per visit half
+// d > cut of the items' hierarchies are visited by one launch per visit half
 // (PRE: zero/smooth nu1/restrict; POST: prolong/smooth nu2) with one CTA per
-// (item, grid) task; everything at or below kDW runs inside one launch (LOW)
-// with one warp per item executing the recursion of Algorithm 1 as a flat
-// program in shared memory.
+// (item, grid) task; everything at or below the cut runs inside one launch
+// (LOW) in which each warp executes the recursion of Algorithm 1 as a flat
+// program in shared memory for a few items of one shape class in lockstep.
 //
 // Storage (all node-indexed with the boundary, see common.cuh):
 //   u64          solution of every grid of every sample (FP64)
@@ -417,154 +417,146 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
 
 // ---------------------------------------------- table-driven low diagonals --
 //
-// Diagonals d <= kDW of an item's hierarchy are visited 2^(L-d) times per
-// cycle (Algorithm 1 with mu = 2) but hold only a few hundred unknowns, so
-// their cost is the latency of the dependent phases, not bandwidth, and the
-// throughput comes from items in flight.  One thread group (a warp, or a CTA
-// of 64/128 threads) owns one item, whose grids with p + q <= kDW + 2 live in
-// shared memory in four compact planes (grids ordered by diagonal):
-//   u   every node of every grid (the boundary stays zero),
-//   b   interior nodes only,
-//   fx  the x-faces (i+1/2, j) of interior rows, fy the y-faces (i, j+1/2) of
-//       interior columns: exactly the coefficients a stencil reads.
-// The mu-cycles run as a flat program of phases.
+// Diagonals d <= dl of an item's hierarchy are visited 2^(L-d) times per cycle
+// (Algorithm 1 with mu = 2) but hold only a few hundred unknowns, so their cost
+// is the latency of a long chain of small dependent phases; throughput comes
+// from items in flight and from keeping lanes busy in the small phases.
 //
-// The program is the recursion of Algorithm 1 unrolled on the host: a list
-// of (phase kind, diagonal) words.  What a phase touches is a table of node
-// entries of its (kind, diagonal) for the item's class; the class is the
-// clipped shape of the triangle, (min(pi, dl+1), min(qi, dl+1), dl), which
-// fixes the grids present and the restriction weights.  Phases are separated
-// by the group's barrier only.
+// One warp runs KW items of the same shape class in lockstep: lane l works on
+// item l / (32/KW) and on every (32/KW)-th table entry of the current phase, so
+// a phase with a single node (the coarsest grid) still occupies KW lanes.  A
+// lane only ever touches its own item's planes, so phases are separated by
+// __syncwarp alone.  Each item's grids with p + q - 2 <= dl live in shared
+// memory in five planes, all in a fixed layout of the full triangle below dl:
+//   u   interior nodes of every grid, red ((i+j) even) then black, row by row,
+//       after one slot (index 0) that stays zero and stands for every boundary
+//       node, so that a stencil reads its neighbours through plain indices;
+//   b   the same indexing as u;
+//   fx  x-faces (i+1/2, j) of interior rows, row by row: the west and east faces
+//       of node (i,j) are neighbours;
+//   fy  y-faces (i, j+1/2) of interior columns, column by column: the south and
+//       north faces of node (i,j) are neighbours;
+//   r   the residual of the diagonal being restricted (row by row per grid).
+// With the red-black order, consecutive entries of a smoothing phase touch
+// consecutive u, b words, and the per-item stride (== 32/KW modulo 32 words)
+// puts the KW items of a warp on disjoint banks.
+//
+// The mu-cycles run as a flat program of phases: the recursion of Algorithm 1
+// unrolled on the host into (kind, diagonal) words and resolved per class of
+// item, the clipped triangle (min(pi, dl+1), min(qi, dl+1), dl), into
+// {kind, entries, first entry}.  An entry is four words of 16-bit indices
+// into the planes.
 
-constexpr int kDW = 4;
-constexpr int kLowWarpsMax = 8;  // items per CTA of the one-warp-per-item variant: 1..8
-constexpr int kLowGrids = (kDW + 1) * (kDW + 2) / 2;
-constexpr int kLowClasses = 55;  // sum over dl = 0..kDW of (dl + 1)^2
+constexpr int kLowMax = 5;  // highest diagonal the low kernel can take
+constexpr int kLowGridsMax = (kLowMax + 1) * (kLowMax + 2) / 2;
+constexpr int kLowClassesMax = 91;  // sum over dl = 0..kLowMax of (dl + 1)^2
+constexpr int kLowWarpsMax = 8;     // warps per CTA of the low kernel
 
-__host__ __device__ constexpr int low_nodes(int p, int q) { return ((1 << p) + 1) * ((1 << q) + 1); }
-// values one grid keeps in the four planes: nodes, interior nodes, x-faces, y-faces
-__host__ __device__ constexpr int low_values(int p, int q)
-{
-    return low_nodes(p, q) + ((1 << p) - 1) * ((1 << q) - 1) + (1 << p) * ((1 << q) - 1) +
-           ((1 << p) - 1) * (1 << q);
-}
-__host__ __device__ constexpr int low_slot()
-{
-    int o = 0;
-    for (int p = 1; p <= kDW + 1; ++p)
-        for (int q = 1; q <= kDW + 2 - p; ++q) o += low_values(p, q);
-    return o;
-}
-constexpr int kLowSlot = low_slot();  // values per item (the full triangle)
+// phase kinds; a resolved program word is {kind | entries << 3, first entry}
+enum LowKind { LK_RED = 0, LK_BLACK, LK_RESID, LK_RESTRICT, LK_PROL, LK_NKIND };
 
-// phase kinds; a program word is kind | diagonal << 3, a resolved program
-// word (per class, empty phases dropped) is {kind | entries << 3, first entry}
-enum LowKind { LK_SMOOTH_RED = 0, LK_SMOOTH_BLACK, LK_RESTRICT, LK_PROL, LK_NKIND };
-
-// Shape class of the triangle below diagonal dl of an item (pic, qic in 1..dl+1).
+// Class of the triangle below diagonal dl of an item (pic, qic in 1..dl+1).
 __host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
 {
     return dl * (dl + 1) * (2 * dl + 1) / 6 + (pic - 1) * (dl + 1) + (qic - 1);
 }
 
-struct LowDesc {
-    int nu, nb, nfx, nfy;         // sizes of the class's four planes
+// Position of interior node (i, j) of a grid with ni = 2^p - 1 interior columns
+// and nj interior rows in the red-black order of the u and b planes (relative
+// to the grid's first slot).  Odd rows hold h + 1 red and h black nodes, even
+// rows h red and h + 1 black, h = (ni - 1) / 2.
+__host__ __device__ __forceinline__ int low_rb(int ni, int nj, int i, int j)
+{
+    const int h = (ni - 1) >> 1;
+    if (((i + j) & 1) == 0) return (j - 1) * h + (j >> 1) + ((i - 1) >> 1);
+    return nj * h + ((nj + 1) >> 1) + (j - 1) * h + ((j - 1) >> 1) + ((i - 1) >> 1);
+}
+
+// Fixed plane layout of the full triangle below dl (independent of the class).
+struct LowGrid {
+    int p, q;
+    int gu;  // first slot of the grid in u and b
+    int gx;  // first x-face in fx
+    int gy;  // first y-face in fy
+};
+struct LowPlanes {
     int dl;
-    int prog, nops;               // resolved program of the class (set per solve)
+    int nu, nfx, nfy, nr;  // plane sizes (nu includes the zero slot)
     int ngrid;
-    int grid[kLowGrids];          // p | q << 4 | first node in u << 8, ordered by diagonal
-    int gb[kLowGrids];            // first interior node of the grid in b
-    int gx[kLowGrids];            // first x-face of the grid in fx
-    int gy[kLowGrids];            // first y-face of the grid in fy
-    int cnt[kDW + 1][LK_NKIND];   // entries of each (diagonal, kind)
-    int off[kDW + 1][LK_NKIND];   // first table word (uint2) of the phase
+    LowGrid g[kLowGridsMax];  // ordered by diagonal, then p
 };
 
-// Where an interior node (i, j) of a grid with row stride W = nx + 1 sits:
-//   u: first + j W + i;  b: gb + (j-1)(W-2) + (i-1)
-//   x-face (i+1/2, j): gx + (j-1)(W-1) + i;  y-face (i, j+1/2): gy + j (W-2) + (i-1)
-// so its stencil reads fx[x-1], fx[x] (west, east) and fy[y], fy[y + W-2]
-// (south, north) with x = its east face and y = its south face.
-//
-// Table entries:
-//   smooth   uint2  x = u | b << 10 | W << 20       y = x-face | y-face << 16
-//   restrict 2 uint2, one per interior node of a child grid on diagonal d-1:
-//            x = child u | child b << 10 | Wc << 20 | has x-parent << 26 | has y-parent << 27
-//            y = x-parent centre u | b << 10 | x-face << 20      (x-parent stride 2 Wc - 1)
-//            z = x-parent centre y-face | y-parent centre u << 10 | b << 20
-//            w = y-parent centre x-face | y-face << 10             (y-parent stride Wc)
-//   prolong  uint2  x = u | W << 10 | i odd << 16 | j odd << 17 | has x-child << 18 |
-//                       has y-child << 19 | x-face << 20
-//                   y = x-child node | y-child node << 10 | y-face << 20
-//            (the child nodes are the coarse u nodes left of / below (i, j))
+struct LowDesc {
+    int dl, pic, qic;
+    int prog, nops;                    // resolved program of the class (set per solve)
+    int cnt[kLowMax + 1][LK_NKIND];    // entries of each (diagonal, kind)
+    int off[kLowMax + 1][LK_NKIND];    // first table entry of the phase
+};
 
-// Residual b - A u at one node (u index c, b index bi, east x-face xf, south y-face yf).
+// One warp's share of a launch: items first .. first + count - 1 of segment seg.
+struct LowTask {
+    int seg, first, count, cls;
+};
+
+// Table entries (16-bit fields, low half first):
+//   smooth / residual  x = c | uw   y = ue | us   z = un | xw   w = ys | r
+//       node c with neighbours uw, ue, us, un (0 on the boundary), west face
+//       xw (east xw + 1), south face ys (north ys + 1), residual slot r;
+//   restrict           x = c | rx   y = ry | wy   z = has x-parent | has y-parent << 1
+//       child node c; x-parent residual around rx (+-1), y-parent around ry (+-wy);
+//   prolong            x = c | xw   y = ys | cx0  z = cx1 | cy0  w = cy1 | has x-child << 16 | has y-child << 17
+//       fine node c; correction 1/2 (u[cx0] + u[cx1]) from the x-child (the two
+//       coincide at even i), likewise from the y-child.
+
 template <class T>
-__host__ __device__ __forceinline__ T low_res(const T* u, const T* b, const T* fx, const T* fy, int c, int bi, int xf,
-                                              int yf, int W)
+__host__ __device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint4 e)
 {
-    T aw = fx[xf - 1], ae = fx[xf], as = fy[yf], an = fy[yf + W - 2];
-    T Au = (aw + ae + as + an) * u[c] - (aw * u[c - 1] + ae * u[c + 1]) - (as * u[c - W] + an * u[c + W]);
-    return b[bi] - Au;
-}
-
-// first table word of a phase for this lane (none past the count)
-__device__ __forceinline__ uint2 low_first(const uint2* ent, uint2 op, int tid)
-{
-    const int kind = op.x & 7, cnt = (int)(op.x >> 3);
-    return tid < cnt ? ent[op.y + (kind == LK_RESTRICT ? 2 * tid : tid)] : make_uint2(0u, 0u);
+    const int c = e.x & 0xFFFF, uw = e.x >> 16, ue = e.y & 0xFFFF, us = e.y >> 16, un = e.z & 0xFFFF;
+    const int xw = e.z >> 16, ys = e.w & 0xFFFF;
+    const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
+    const T nb = (aw * u[uw] + ae * u[ue]) + (as * u[us] + an * u[un]);
+    u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
 }
 
 template <class T>
-__host__ __device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint2 e)
+__host__ __device__ __forceinline__ void low_resid(const T* u, const T* b, const T* fx, const T* fy, T* r, uint4 e)
 {
-    const int c = e.x & 0x3FF, bi = (e.x >> 10) & 0x3FF, W = e.x >> 20, xf = e.y & 0xFFFF, yf = e.y >> 16;
-    T aw = fx[xf - 1], ae = fx[xf], as = fy[yf], an = fy[yf + W - 2];
-    T nb = (aw * u[c - 1] + ae * u[c + 1]) + (as * u[c - W] + an * u[c + W]);
-    u[c] = (b[bi] + nb) * rcp_of(aw + ae + as + an);
+    const int c = e.x & 0xFFFF, uw = e.x >> 16, ue = e.y & 0xFFFF, us = e.y >> 16, un = e.z & 0xFFFF;
+    const int xw = e.z >> 16, ys = e.w & 0xFFFF;
+    const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
+    const T Au = (aw + ae + as + an) * u[c] - (aw * u[uw] + ae * u[ue]) - (as * u[us] + an * u[un]);
+    r[e.w >> 16] = b[c] - Au;
 }
 
 // Eq. (2.3) for one child node: b = R_x r of the x-parent and/or R_y r of the
 // y-parent, averaged when it has both; the child's correction restarts from 0
 // (the recursion's first visit of the child follows every restriction).
-// The three x-parent nodes are neighbours in one row (every index +-1), the
-// three y-parent nodes in one column (u +-Wc, b and y-face +-(Wc-2), x-face +-(Wc-1)).
 template <class T>
-__host__ __device__ __forceinline__ void low_restrict(T* u, T* b, const T* fx, const T* fy, uint2 e, uint2 f)
+__host__ __device__ __forceinline__ void low_restrict(T* u, T* b, const T* r, uint4 e)
 {
-    const int cu = e.x & 0x3FF, cb = (e.x >> 10) & 0x3FF, Wc = (e.x >> 20) & 0x3F;
-    const bool hx = (e.x >> 26) & 1, hy = (e.x >> 27) & 1;
+    const int c = e.x & 0xFFFF, rx = e.x >> 16, ry = e.y & 0xFFFF, wy = e.y >> 16;
+    const bool hx = e.z & 1, hy = e.z & 2;
     T vx = T(0), vy = T(0);
-    if (hx) {
-        const int pu = e.y & 0x3FF, pb = (e.y >> 10) & 0x3FF, px = e.y >> 20, py = f.x & 0x3FF, W = 2 * Wc - 1;
-        vx = T(0.25) * (low_res(u, b, fx, fy, pu - 1, pb - 1, px - 1, py - 1, W) +
-                        T(2) * low_res(u, b, fx, fy, pu, pb, px, py, W) +
-                        low_res(u, b, fx, fy, pu + 1, pb + 1, px + 1, py + 1, W));
-    }
-    if (hy) {
-        const int qu = (f.x >> 10) & 0x3FF, qb = f.x >> 20, qx = f.y & 0x3FF, qy = f.y >> 10, W = Wc;
-        vy = T(0.25) * (low_res(u, b, fx, fy, qu - W, qb - (W - 2), qx - (W - 1), qy - (W - 2), W) +
-                        T(2) * low_res(u, b, fx, fy, qu, qb, qx, qy, W) +
-                        low_res(u, b, fx, fy, qu + W, qb + (W - 2), qx + (W - 1), qy + (W - 2), W));
-    }
-    b[cb] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
-    u[cu] = T(0);
+    if (hx) vx = T(0.25) * (r[rx - 1] + T(2) * r[rx] + r[rx + 1]);
+    if (hy) vy = T(0.25) * (r[ry - wy] + T(2) * r[ry] + r[ry + wy]);
+    b[c] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+    u[c] = T(0);
 }
 
+// Eq. (2.4) with linear P and the kappa weights of Eq. (2.5).
 template <class T>
-__host__ __device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint2 e, T omega)
+__host__ __device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint4 e, T omega)
 {
-    const int c = e.x & 0x3FF, W = (e.x >> 10) & 0x3F, xf = e.x >> 20;
-    const bool iodd = (e.x >> 16) & 1, jodd = (e.x >> 17) & 1;
-    const bool hx = (e.x >> 18) & 1, hy = (e.x >> 19) & 1;
-    const int rx = e.y & 0x3FF, ry = (e.y >> 10) & 0x3FF, yf = e.y >> 20;
+    const int c = e.x & 0xFFFF, xw = e.x >> 16, ys = e.y & 0xFFFF;
+    const int cx0 = e.y >> 16, cx1 = e.z & 0xFFFF, cy0 = e.z >> 16, cy1 = e.w & 0xFFFF;
+    const bool hx = (e.w >> 16) & 1, hy = (e.w >> 17) & 1;
     T vx = T(0), vy = T(0);
-    if (hx) vx = iodd ? T(0.5) * (u[rx] + u[rx + 1]) : u[rx];
-    if (hy) vy = jodd ? T(0.5) * (u[ry] + u[ry + W]) : u[ry];
+    if (hx) vx = T(0.5) * (u[cx0] + u[cx1]);
+    if (hy) vy = T(0.5) * (u[cy0] + u[cy1]);
     T corr;
     if (hx && hy) {
-        T cxv = fx[xf - 1] + fx[xf], cyv = fy[yf] + fy[yf + W - 2];
-        T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+        const T cxv = fx[xw] + fx[xw + 1], cyv = fy[ys] + fy[ys + 1];
+        const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
         corr = (x2 * s) * vx + (y2 * s) * vy;
     } else {
         corr = hx ? vx : vy;
@@ -572,107 +564,125 @@ __host__ __device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy
     u[c] += omega * corr;
 }
 
-template <int NT>
-__device__ __forceinline__ void low_sync()
+// One phase of the program for one item (the lane's share of its entries).
+template <class T>
+__host__ __device__ __forceinline__ void low_phase(int kind, T* u, T* b, const T* fx, const T* fy, T* r, uint4 e,
+                                                   T omega)
 {
-    if constexpr (NT == 32) __syncwarp();
-    else __syncthreads();
+    if (kind <= LK_BLACK) low_smooth(u, b, fx, fy, e);
+    else if (kind == LK_RESID) low_resid(u, b, fx, fy, r, e);
+    else if (kind == LK_RESTRICT) low_restrict(u, b, r, e);
+    else low_prol(u, fx, fy, e, omega);
 }
 
-// `calls` mu-cycles at diagonal dl <= kDW of each item, starting from zero.
-// NT = 32: blockDim.x / 32 items per CTA, one warp each; NT > 32: one item per
-// CTA of NT threads.  Reads the coefficients of the item's grids with
-// d <= dl and the right-hand side of its diagonal-dl grids (combined from the
-// parents' restrictions, or the item's own residual when dl is its top);
-// writes back u of diagonal dl.
-template <class T, int NT>
-__global__ void __launch_bounds__(256, 4) k_low(DevCtx cx, int64_t nitems, T* su, const T* sbx, const T* sby,
-                                             const T* ax, const T* ay, const LowDesc* descs, const uint2* ent,
-                                             const uint2* rprog, int dl, int calls, CycleParams cp)
+__device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_t local)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int slot = threadIdx.x / NT, tid = threadIdx.x % NT;
-    const int64_t it = (int64_t)blockIdx.x * (blockDim.x / NT) + slot;
-    if (it >= nitems) return;  // a whole warp (NT = 32) or the whole CTA (NT > 32)
-    const TaskRef t = resolve_at(cx, it);
+    const Segment* sg = &cx.segs[seg];
+    const Group& G = cx.groups[sg->g];
+    TaskRef t;
+    t.s = cx.slist[sg->list_off + local];
+    t.seg = sg;
+    const int gp = cx.gpos[t.s];
+    t.scr = G.scr_start + (int64_t)gp * G.scr_per_sample + sg->scr_slot;
     const SampleInfo& S = cx.samples[t.s];
-    const int pi = t.seg->pi, qi = t.seg->qi;
-    const LowDesc& C = descs[low_class(min(pi, dl + 1), min(qi, dl + 1), dl)];
-    T* u = (T*)smem_raw + (size_t)slot * kLowSlot;
-    T* b = u + C.nu;
-    T* fx = b + C.nb;
-    T* fy = fx + C.nfx;
-    for (int k = tid; k < C.nu; k += NT) u[k] = T(0);
-    for (int g = 0; g < C.ngrid; ++g) {
-        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, nx = 1 << p, W = nx + 1;
-        const int64_t co = S.node_off + grid_offset(p, q, S.Q);
-        // x-faces (i+1/2, j) of rows j = 1..ny-1, stored at node (i, j)
-        const int nxf = ((1 << q) - 1) << p;
-        for (int k = tid; k < nxf; k += NT) {
-            const int i = k & (nx - 1), j = 1 + (k >> p);
-            fx[C.gx[g] + k] = ax[co + j * W + i];
-        }
-        // y-faces (i, j+1/2) of columns i = 1..nx-1, stored at node (i, j); slot i = 0 is skipped
-        const int nyf = (1 << q) << p;
-        for (int k = tid; k < nyf; k += NT) {
-            const int i = k & (nx - 1), j = k >> p;
-            if (i == 0) continue;
-            fy[C.gy[g] + j * (nx - 1) + (i - 1)] = ay[co + j * W + i];
-        }
-        if (p + q - 2 == dl) {  // b at the interior nodes
-            const int64_t so = t.scr + grid_offset(p, q, qi);
-            const bool hx = p < pi, hy = q < qi;
-            for (int k = tid; k < nxf; k += NT) {
-                const int i = k & (nx - 1), j = 1 + (k >> p);
-                if (i == 0) continue;
-                const int64_t n = so + j * W + i;
-                T v;
-                if (hx && hy) v = T(0.5) * sbx[n] + T(0.5) * sby[n];
-                else if (hy) v = sby[n];
-                else v = sbx[n];  // x-parent only, or the item's own residual
-                b[C.gb[g] + (j - 1) * (nx - 1) + (i - 1)] = v;
+    t.item = S.q_off + (int64_t)(sg->pi - 1) * S.Q + (sg->qi - 1);
+    t.sidx = sg->stage_base + gp;
+    return t;
+}
+
+// `calls` mu-cycles at diagonal lp.dl of each item, starting from zero.
+// Reads the coefficients of the item's grids with d <= dl and the right-hand
+// side of its diagonal-dl grids (combined from the parents' restrictions, or the
+// item's own residual when dl is its top); writes back u of diagonal dl.
+template <class T, int KW>
+__global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const LowTask* tasks, int ntasks, T* su,
+                                                           const T* sbx, const T* sby, const T* ax, const T* ay,
+                                                           const LowDesc* descs, const uint4* ent,
+                                                           const uint2* rprog, LowPlanes lp, int stride, int calls,
+                                                           T omega)
+{
+    constexpr int EW = 32 / KW;  // lanes per item
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (gw >= ntasks) return;  // the whole warp
+    const LowTask tk = tasks[gw];
+    const int k = lane / EW, el = lane % EW;
+    const bool act = k < tk.count;
+    T* u = (T*)smem_raw + ((size_t)warp * KW + k) * stride;
+    T* b = u + lp.nu;
+    T* fx = b + lp.nu;
+    T* fy = fx + lp.nfx;
+    T* r = fy + lp.nfy;
+    const LowDesc& D = descs[tk.cls];
+    const int dl = lp.dl;
+    if (act) {
+        const TaskRef t = resolve_seg(cx, tk.seg, tk.first + k);
+        const SampleInfo& S = cx.samples[t.s];
+        const int pi = t.seg->pi, qi = t.seg->qi;
+        for (int v = el; v < lp.nu; v += EW) u[v] = T(0);
+        for (int g = 0; g < lp.ngrid; ++g) {
+            const LowGrid G = lp.g[g];
+            const int p = G.p, q = G.q;
+            if (p > D.pic || q > D.qic) continue;
+            const int nx = 1 << p, ny = 1 << q, W = nx + 1;
+            const int64_t co = S.node_off + grid_offset(p, q, S.Q);
+            const int nxf = (ny - 1) << p;  // x-faces (i+1/2, j), j = 1..ny-1, stored at node (i, j)
+            for (int v = el; v < nxf; v += EW) {
+                const int i = v & (nx - 1), j = 1 + (v >> p);
+                fx[G.gx + v] = ax[co + j * W + i];
             }
-        }
-    }
-    low_sync<NT>();
-    const T omega = (T)cp.omega;
-    const uint2* rp = rprog + C.prog;
-    const int nops = C.nops;
-    for (int call = 0; call < calls; ++call) {
-        // software pipeline: the words of the next two phases and this lane's
-        // first table word of the next phase are in flight while a phase runs
-        uint2 op = nops > 0 ? rp[0] : make_uint2(0u, 0u);
-        uint2 op1 = nops > 1 ? rp[1] : make_uint2(0u, 0u);
-        uint2 e = low_first(ent, op, tid);
-        for (int o = 0; o < nops; ++o) {
-            const uint2 op2 = o + 2 < nops ? rp[o + 2] : make_uint2(0u, 0u);
-            const uint2 e1 = low_first(ent, op1, tid);
-            const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
-            if (tid < cnt) {
-                if (kind <= LK_SMOOTH_BLACK) {
-                    low_smooth(u, b, fx, fy, e);
-                    for (int k = tid + NT; k < cnt; k += NT) low_smooth(u, b, fx, fy, ent[off + k]);
-                } else if (kind == LK_RESTRICT) {
-                    low_restrict(u, b, fx, fy, e, ent[off + 2 * tid + 1]);
-                    for (int k = tid + NT; k < cnt; k += NT)
-                        low_restrict(u, b, fx, fy, ent[off + 2 * k], ent[off + 2 * k + 1]);
-                } else {
-                    low_prol(u, fx, fy, e, omega);
-                    for (int k = tid + NT; k < cnt; k += NT) low_prol(u, fx, fy, ent[off + k], omega);
+            const int nyf = ny << p;  // y-faces (i, j+1/2), i = 1..nx-1, column by column
+            for (int v = el; v < nyf; v += EW) {
+                const int i = v & (nx - 1), j = v >> p;
+                if (i == 0) continue;
+                fy[G.gy + (i - 1) * ny + j] = ay[co + j * W + i];
+            }
+            if (p + q - 2 == dl) {  // b at the interior nodes
+                const int64_t so = t.scr + grid_offset(p, q, qi);
+                const bool hx = p < pi, hy = q < qi;
+                for (int v = el; v < nxf; v += EW) {
+                    const int i = v & (nx - 1), j = 1 + (v >> p);
+                    if (i == 0) continue;
+                    const int64_t n = so + j * W + i;
+                    T val;
+                    if (hx && hy) val = T(0.5) * sbx[n] + T(0.5) * sby[n];
+                    else if (hy) val = sby[n];
+                    else val = sbx[n];  // x-parent only, or the item's own residual
+                    b[G.gu + low_rb(nx - 1, ny - 1, i, j)] = val;
                 }
             }
-            low_sync<NT>();
-            op = op1;
-            op1 = op2;
-            e = e1;
         }
     }
-    for (int g = 0; g < C.ngrid; ++g) {
-        const int w = C.grid[g], p = w & 15, q = (w >> 4) & 15, o = w >> 8;
-        if (p + q - 2 != dl) continue;
-        T* dst = su + t.scr + grid_offset(p, q, qi);
-        const int n = low_nodes(p, q);
-        for (int k = tid; k < n; k += NT) dst[k] = u[o + k];
+    __syncwarp();
+    const uint2* rp = rprog + D.prog;
+    const int nops = D.nops;
+    for (int call = 0; call < calls; ++call) {
+        uint2 op = nops > 0 ? rp[0] : make_uint2(0u, 0u);
+        for (int o = 0; o < nops; ++o) {
+            const uint2 nxt = o + 1 < nops ? rp[o + 1] : make_uint2(0u, 0u);
+            const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
+            if (act)
+                for (int e = el; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, ent[off + e], omega);
+            __syncwarp();
+            op = nxt;
+        }
+    }
+    if (act) {
+        const TaskRef t = resolve_seg(cx, tk.seg, tk.first + k);
+        const int qi = t.seg->qi;
+        for (int g = 0; g < lp.ngrid; ++g) {
+            const LowGrid G = lp.g[g];
+            const int p = G.p, q = G.q;
+            if (p + q - 2 != dl || p > D.pic || q > D.qic) continue;
+            const int nx = 1 << p, ny = 1 << q, W = nx + 1, n = W * (ny + 1);
+            T* dst = su + t.scr + grid_offset(p, q, qi);
+            for (int v = el; v < n; v += EW) {
+                const int j = v / W, i = v - j * W;
+                const bool in = i > 0 && i < nx && j > 0 && j < ny;
+                dst[v] = in ? u[G.gu + low_rb(nx - 1, ny - 1, i, j)] : T(0);
+            }
+        }
     }
 }
 
@@ -912,98 +922,134 @@ struct ItemType {
 
 // ------------------------------------------------ low-diagonal host tables --
 
-// Tables of every class (independent of the solver parameters).
+// Fixed plane layout of the full triangle below dl.
+static LowPlanes low_planes(int dl)
+{
+    LowPlanes L;
+    std::memset(&L, 0, sizeof(L));
+    L.dl = dl;
+    L.nu = 1;  // slot 0: the zero that stands for boundary nodes
+    for (int d = 0; d <= dl; ++d) {
+        int nr = 0;
+        for (int p = 1; p <= d + 1; ++p) {
+            const int q = d + 2 - p, nx = 1 << p, ny = 1 << q;
+            LowGrid& G = L.g[L.ngrid++];
+            G.p = p;
+            G.q = q;
+            G.gu = L.nu;
+            G.gx = L.nfx;
+            G.gy = L.nfy;
+            L.nu += (nx - 1) * (ny - 1);
+            L.nfx += nx * (ny - 1);
+            L.nfy += (nx - 1) * ny;
+            nr += (nx - 1) * (ny - 1);
+        }
+        L.nr = std::max(L.nr, nr);
+    }
+    return L;
+}
+
+// values of one item's planes (u, b, fx, fy, r)
+static int low_values(const LowPlanes& L) { return 2 * L.nu + L.nfx + L.nfy + L.nr; }
+
+// Shared-memory stride of one item: at least its values, and congruent to the
+// lanes per item (32/kw) modulo the bank count so that the kw items of a warp
+// sit on disjoint banks (4-byte banks; 16 bank pairs for 8-byte words).
+static int low_stride(const LowPlanes& L, int kw, size_t es)
+{
+    const int ew = 32 / kw, m = es == 4 ? 32 : 16;
+    const int v = low_values(L);
+    return (v + m - 1) / m * m + (ew % m);
+}
+
 struct LowTables {
-    std::vector<LowDesc> desc;  // [kLowClasses]
-    std::vector<uint2> ent;
+    std::vector<LowPlanes> planes;  // [dl]
+    std::vector<LowDesc> desc;      // [class]
+    std::vector<uint4> ent;
 };
 
-static void low_build_class(int pic, int qic, int dl, LowDesc& D, std::vector<uint2>& ent)
+static void low_build_class(int pic, int qic, int dl, const LowPlanes& L, LowDesc& D, std::vector<uint4>& ent)
 {
     std::memset(&D, 0, sizeof(D));
     D.dl = dl;
-    int gu[kDW + 3][kDW + 3], gb[kDW + 3][kDW + 3], gx[kDW + 3][kDW + 3], gy[kDW + 3][kDW + 3];
+    D.pic = pic;
+    D.qic = qic;
     auto exists = [&](int p, int q) { return p >= 1 && q >= 1 && p <= pic && q <= qic && p + q - 2 <= dl; };
-    for (int d = 0; d <= dl; ++d)
-        for (int p = 1; p <= d + 1; ++p) {
-            const int q = d + 2 - p;
-            if (!exists(p, q)) continue;
-            const int nx = 1 << p, ny = 1 << q;
-            gu[p][q] = D.nu;
-            gb[p][q] = D.nb;
-            gx[p][q] = D.nfx;
-            gy[p][q] = D.nfy;
-            D.grid[D.ngrid] = p | q << 4 | D.nu << 8;
-            D.gb[D.ngrid] = D.nb;
-            D.gx[D.ngrid] = D.nfx;
-            D.gy[D.ngrid] = D.nfy;
-            ++D.ngrid;
-            D.nu += low_nodes(p, q);
-            D.nb += (nx - 1) * (ny - 1);
-            D.nfx += nx * (ny - 1);
-            D.nfy += (nx - 1) * ny;
+    auto grid = [&](int p, int q) -> const LowGrid& {
+        for (int k = 0; k < L.ngrid; ++k)
+            if (L.g[k].p == p && L.g[k].q == q) return L.g[k];
+        return L.g[0];  // not reached for grids of the triangle
+    };
+    // u/b slot of node (i, j) of grid (p, q); 0 on the boundary
+    auto U = [&](int p, int q, int i, int j) -> uint32_t {
+        const int nx = 1 << p, ny = 1 << q;
+        if (i <= 0 || i >= nx || j <= 0 || j >= ny) return 0u;
+        return (uint32_t)(grid(p, q).gu + low_rb(nx - 1, ny - 1, i, j));
+    };
+    // residual slot of interior node (i, j) of grid (p, q) on its diagonal (grids in p order)
+    auto R = [&](int p, int q, int i, int j) -> uint32_t {
+        int o = 0;
+        for (int pp = 1; pp < p; ++pp) {
+            const int qq = p + q - pp;
+            if (exists(pp, qq)) o += ((1 << pp) - 1) * ((1 << qq) - 1);
         }
-    // indices of interior node (i, j) of grid (p, q) in the four planes
-    auto U = [&](int p, int q, int i, int j) { return (uint32_t)(gu[p][q] + j * ((1 << p) + 1) + i); };
-    auto B = [&](int p, int q, int i, int j) { return (uint32_t)(gb[p][q] + (j - 1) * ((1 << p) - 1) + (i - 1)); };
-    auto X = [&](int p, int q, int i, int j) { return (uint32_t)(gx[p][q] + (j - 1) * (1 << p) + i); };
-    auto Y = [&](int p, int q, int i, int j) { return (uint32_t)(gy[p][q] + (j - 1) * ((1 << p) - 1) + (i - 1)); };
+        return (uint32_t)(o + (j - 1) * ((1 << p) - 1) + (i - 1));
+    };
+    auto XW = [&](int p, int q, int i, int j) { return (uint32_t)(grid(p, q).gx + (j - 1) * (1 << p) + (i - 1)); };
+    auto YS = [&](int p, int q, int i, int j) { return (uint32_t)(grid(p, q).gy + (i - 1) * (1 << q) + (j - 1)); };
     for (int d = 0; d <= dl; ++d) {
-        for (int colour = 0; colour < 2; ++colour) {  // red: (i + j) even
-            D.off[d][LK_SMOOTH_RED + colour] = (int)ent.size();
+        // red then black entries of every grid of the diagonal, contiguous: the
+        // residual phase runs over both lists at once
+        for (int colour = 0; colour < 2; ++colour) {
+            D.off[d][LK_RED + colour] = (int)ent.size();
             for (int p = 1; p <= d + 1; ++p) {
                 const int q = d + 2 - p;
                 if (!exists(p, q)) continue;
-                const int nx = 1 << p, ny = 1 << q, W = nx + 1;
+                const int nx = 1 << p, ny = 1 << q;
                 for (int j = 1; j < ny; ++j)
                     for (int i = 1; i < nx; ++i)
                         if (((i + j) & 1) == colour)
-                            ent.push_back(make_uint2(U(p, q, i, j) | B(p, q, i, j) << 10 | (uint32_t)W << 20,
-                                                     X(p, q, i, j) | Y(p, q, i, j) << 16));
+                            ent.push_back(make_uint4(U(p, q, i, j) | U(p, q, i - 1, j) << 16,
+                                                     U(p, q, i + 1, j) | U(p, q, i, j - 1) << 16,
+                                                     U(p, q, i, j + 1) | XW(p, q, i, j) << 16,
+                                                     YS(p, q, i, j) | R(p, q, i, j) << 16));
             }
-            D.cnt[d][LK_SMOOTH_RED + colour] = (int)ent.size() - D.off[d][LK_SMOOTH_RED + colour];
+            D.cnt[d][LK_RED + colour] = (int)ent.size() - D.off[d][LK_RED + colour];
         }
+        D.off[d][LK_RESID] = D.off[d][LK_RED];
+        D.cnt[d][LK_RESID] = D.cnt[d][LK_RED] + D.cnt[d][LK_BLACK];
         if (d == 0) continue;
-        // Eq. (2.3), one entry (two words) per interior node (i, j) of each child
-        // (p, q) on diagonal d-1: R_x from the x-parent (p+1, q) around its node
-        // (2i, j), R_y from the y-parent (p, q+1) around its node (i, 2j)
+        // Eq. (2.3), one entry per interior node (i, j) of each child (p, q) on
+        // diagonal d-1: R_x from the x-parent (p+1, q) around its node (2i, j),
+        // R_y from the y-parent (p, q+1) around its node (i, 2j)
         D.off[d][LK_RESTRICT] = (int)ent.size();
-        int nr = 0;
         for (int p = 1; p <= d; ++p) {
             const int q = d + 1 - p;
             if (!exists(p, q)) continue;
             const bool hx = exists(p + 1, q), hy = exists(p, q + 1);
             if (!hx && !hy) continue;  // only in classes no item has (pic + qic < dl + 2)
-            const int nx = 1 << p, ny = 1 << q, Wc = nx + 1;
+            const int nx = 1 << p, ny = 1 << q;
             for (int j = 1; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) {
-                    const uint32_t pu = hx ? U(p + 1, q, 2 * i, j) : 0u, pb = hx ? B(p + 1, q, 2 * i, j) : 0u;
-                    const uint32_t px = hx ? X(p + 1, q, 2 * i, j) : 0u, py = hx ? Y(p + 1, q, 2 * i, j) : 0u;
-                    const uint32_t qu = hy ? U(p, q + 1, i, 2 * j) : 0u, qb = hy ? B(p, q + 1, i, 2 * j) : 0u;
-                    const uint32_t qx = hy ? X(p, q + 1, i, 2 * j) : 0u, qy = hy ? Y(p, q + 1, i, 2 * j) : 0u;
-                    ent.push_back(make_uint2(U(p, q, i, j) | B(p, q, i, j) << 10 | (uint32_t)Wc << 20 |
-                                                 (uint32_t)hx << 26 | (uint32_t)hy << 27,
-                                             pu | pb << 10 | px << 20));
-                    ent.push_back(make_uint2(py | qu << 10 | qb << 20, qx | qy << 10));
-                    ++nr;
+                    const uint32_t rx = hx ? R(p + 1, q, 2 * i, j) : 0u, ry = hy ? R(p, q + 1, i, 2 * j) : 0u;
+                    ent.push_back(make_uint4(U(p, q, i, j) | rx << 16, ry | (uint32_t)(nx - 1) << 16,
+                                             (uint32_t)hx | (uint32_t)hy << 1, 0u));
                 }
         }
-        D.cnt[d][LK_RESTRICT] = nr;
+        D.cnt[d][LK_RESTRICT] = (int)ent.size() - D.off[d][LK_RESTRICT];
         // Eq. (2.4)/(2.5): linear prolongation from each child, kappa-weighted
         D.off[d][LK_PROL] = (int)ent.size();
         for (int p = 1; p <= d + 1; ++p) {
             const int q = d + 2 - p;
             if (!exists(p, q)) continue;
-            const int nx = 1 << p, ny = 1 << q, W = nx + 1, Wc = (nx >> 1) + 1;
+            const int nx = 1 << p, ny = 1 << q;
             const bool hx = p > 1, hy = q > 1;
             for (int j = 1; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) {
-                    const uint32_t rx = hx ? (uint32_t)(gu[p - 1][q] + j * Wc + (i >> 1)) : 0u;
-                    const uint32_t ry = hy ? (uint32_t)(gu[p][q - 1] + (j >> 1) * W + i) : 0u;
-                    ent.push_back(make_uint2(U(p, q, i, j) | (uint32_t)W << 10 | (uint32_t)(i & 1) << 16 |
-                                                 (uint32_t)(j & 1) << 17 | (uint32_t)hx << 18 | (uint32_t)hy << 19 |
-                                                 X(p, q, i, j) << 20,
-                                             rx | ry << 10 | Y(p, q, i, j) << 20));
+                    const uint32_t cx0 = hx ? U(p - 1, q, i >> 1, j) : 0u, cx1 = hx ? U(p - 1, q, (i + 1) >> 1, j) : 0u;
+                    const uint32_t cy0 = hy ? U(p, q - 1, i, j >> 1) : 0u, cy1 = hy ? U(p, q - 1, i, (j + 1) >> 1) : 0u;
+                    ent.push_back(make_uint4(U(p, q, i, j) | XW(p, q, i, j) << 16, YS(p, q, i, j) | cx0 << 16,
+                                             cx1 | cy0 << 16, cy1 | (uint32_t)hx << 16 | (uint32_t)hy << 17));
                 }
         }
         D.cnt[d][LK_PROL] = (int)ent.size() - D.off[d][LK_PROL];
@@ -1014,31 +1060,34 @@ static const LowTables& low_tables()
 {
     static const LowTables tabs = [] {
         LowTables t;
-        t.desc.resize(kLowClasses);
-        for (int dl = 0; dl <= kDW; ++dl)
+        for (int dl = 0; dl <= kLowMax; ++dl) t.planes.push_back(low_planes(dl));
+        t.desc.resize(kLowClassesMax);
+        for (int dl = 0; dl <= kLowMax; ++dl)
             for (int pic = 1; pic <= dl + 1; ++pic)
-                for (int qic = 1; qic <= dl + 1; ++qic) low_build_class(pic, qic, dl, t.desc[low_class(pic, qic, dl)], t.ent);
+                for (int qic = 1; qic <= dl + 1; ++qic)
+                    low_build_class(pic, qic, dl, t.planes[dl], t.desc[low_class(pic, qic, dl)], t.ent);
         return t;
     }();
     return tabs;
 }
 
 // Algorithm 1 below diagonal dl as a flat program (the recursion unrolled): the
-// visit of diagonal d smooths nu1 times, restricts to diagonal d-1 (which also
-// restarts the correction there from zero for the first of the mu visits),
-// recurses mu times, prolongs and smooths nu2 times.  Diagonal 0 is solved
-// exactly (one unknown, u = b / A); its b does not change between the mu
-// visits of one parent visit, so the repeats, which would write the same
-// value, are left out.  The kernel starts every item from u = 0.
+// visit of diagonal d smooths nu1 times, forms the residual and restricts it to
+// diagonal d-1 (which also restarts the correction there from zero for the
+// first of the mu visits), recurses mu times, prolongs and smooths nu2 times.
+// Diagonal 0 is solved exactly (one unknown, u = b / A); its b does not change
+// between the mu visits of one parent visit, so the repeats, which would write
+// the same value, are left out.  The kernel starts every item from u = 0.
 static void low_program_rec(int d, const msg_params& prm, std::vector<int>& prog)
 {
     auto emit = [&](int kind, int dd) { prog.push_back(kind | dd << 3); };
-    if (d == 0) { emit(LK_SMOOTH_RED, 0); return; }
-    for (int s = 0; s < prm.nu1; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
+    if (d == 0) { emit(LK_RED, 0); return; }
+    for (int s = 0; s < prm.nu1; ++s) { emit(LK_RED, d); emit(LK_BLACK, d); }
+    emit(LK_RESID, d);
     emit(LK_RESTRICT, d);
     for (int k = 0; k < (d == 1 ? 1 : prm.mu); ++k) low_program_rec(d - 1, prm, prog);
     emit(LK_PROL, d);
-    for (int s = 0; s < prm.nu2; ++s) { emit(LK_SMOOTH_RED, d); emit(LK_SMOOTH_BLACK, d); }
+    for (int s = 0; s < prm.nu2; ++s) { emit(LK_RED, d); emit(LK_BLACK, d); }
 }
 
 static std::vector<int> low_program(int dl, const msg_params& prm)
@@ -1049,23 +1098,48 @@ static std::vector<int> low_program(int dl, const msg_params& prm)
 }
 
 // Resolved programs of every class for these parameters: each (kind, diagonal)
-// word becomes {kind | entries << 3, first entry} of the class, phases with no
-// entries are dropped; desc[c].prog / nops locate class c's program.
+// word becomes {kind | entries << 3, first entry} of the class; phases with no
+// entries are dropped, and so is a residual phase whose restriction is empty.
 static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc)
 {
     desc = low_tables().desc;
-    std::vector<int> words[kDW + 1];
-    for (int dl = 0; dl <= kDW; ++dl) words[dl] = low_program(dl, prm);
+    std::vector<int> words[kLowMax + 1];
+    for (int dl = 0; dl <= kLowMax; ++dl) words[dl] = low_program(dl, prm);
     std::vector<uint2> rp;
     for (LowDesc& D : desc) {
         D.prog = (int)rp.size();
+        if (D.pic == 0) { D.nops = 0; continue; }
         for (int w : words[D.dl]) {
             const int kind = w & 7, d = w >> 3, cnt = D.cnt[d][kind];
-            if (cnt > 0) rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)D.off[d][kind]));
+            if (cnt == 0) continue;
+            if (kind == LK_RESID && D.cnt[d][LK_RESTRICT] == 0) continue;
+            rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)D.off[d][kind]));
         }
         D.nops = (int)rp.size() - D.prog;
     }
     return rp;
+}
+
+constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory of one CTA
+// Launch shape and cut of the low-diagonal kernel for these parameters.
+struct LowShape {
+    int cut;    // diagonals <= cut of a hierarchy run inside one k_lowv launch
+    int items;  // items per warp (KW)
+    int warps;  // warps per CTA
+    int stride; // shared-memory values per item
+    size_t smem;  // bytes per CTA
+};
+static LowShape low_shape(const msg_params& prm)
+{
+    const bool mixed = prm.precision == MSG_PREC_MIXED;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    LowShape s;
+    s.cut = prm.tune_low_cut ? prm.tune_low_cut : (mixed ? 5 : 4);
+    s.items = prm.tune_low_items ? prm.tune_low_items : (mixed ? 2 : 2);
+    s.warps = prm.tune_low_warps ? prm.tune_low_warps : 2;
+    s.stride = low_stride(low_tables().planes[s.cut], s.items, es);
+    s.smem = es * (size_t)s.stride * s.items * s.warps;
+    return s;
 }
 
 struct Plan {
@@ -1104,13 +1178,21 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         set_error("tune_block must be 0 or a multiple of 32 in [32, 1024]");
         return MSG_ERR_INVALID;
     }
-    if (prm->tune_low_threads != 0 && prm->tune_low_threads != 32 && prm->tune_low_threads != 64 &&
-        prm->tune_low_threads != 128) {
-        set_error("tune_low_threads must be 0, 32, 64 or 128");
+    if (prm->tune_low_items != 0 && prm->tune_low_items != 1 && prm->tune_low_items != 2 &&
+        prm->tune_low_items != 4 && prm->tune_low_items != 8) {
+        set_error("tune_low_items must be 0, 1, 2, 4 or 8");
         return MSG_ERR_INVALID;
     }
     if (prm->tune_low_warps < 0 || prm->tune_low_warps > kLowWarpsMax) {
         set_error("tune_low_warps must be in [0, 8]");
+        return MSG_ERR_INVALID;
+    }
+    if (prm->tune_low_cut < 0 || prm->tune_low_cut > kLowMax) {
+        set_error("tune_low_cut must be in [0, 5]");
+        return MSG_ERR_INVALID;
+    }
+    if (low_shape(*prm).smem > kSmemMax) {
+        set_error("tune_low_warps x tune_low_items items of the low-diagonal kernel do not fit the shared memory of one CTA");
         return MSG_ERR_INVALID;
     }
     if (prm->coef != MSG_COEF_SERIES && prm->coef != MSG_COEF_INJECT) {
@@ -1215,7 +1297,7 @@ struct WsLayout {
     size_t u64, ax64, ay64, ax32, ay32;
     size_t low_desc, low_ent, low_prog;  // tables of the low-diagonal program
     // per stage L: segment list, sample list, flags, counter, scratch (su, sbx, sby)
-    std::vector<size_t> segs, slist, sflag, counter, su, sbx, sby;
+    std::vector<size_t> segs, tasks, slist, sflag, counter, su, sbx, sby;
     size_t total;
 };
 
@@ -1232,8 +1314,8 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
     w.allsegs = take(sizeof(Segment) * pl.all_segs.size());
     {
         std::vector<LowDesc> desc;
-        w.low_desc = take(sizeof(LowDesc) * kLowClasses);
-        w.low_ent = take(sizeof(uint2) * low_tables().ent.size());
+        w.low_desc = take(sizeof(LowDesc) * kLowClassesMax);
+        w.low_ent = take(sizeof(uint4) * low_tables().ent.size());
         w.low_prog = take(sizeof(uint2) * low_resolve(prm, desc).size());
     }
     w.nstep = take(sizeof(int) * pl.total_q);
@@ -1252,6 +1334,7 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
         for (const ItemType& it : pl.stage_items[L]) nseg += 1 + (int64_t)it.pi * it.qi;
         for (const Group& g : pl.stage_groups[L]) scr += g.scr_per_sample * g.count;
         w.segs.push_back(take(sizeof(Segment) * nseg));
+        w.tasks.push_back(take(sizeof(LowTask) * (pl.stage_nitems[L] + pl.stage_items[L].size())));
         w.slist.push_back(take(sizeof(int) * pl.stage_nitems[L]));
         w.sflag.push_back(take(sizeof(int) * pl.stage_nitems[L]));
         w.counter.push_back(take(sizeof(int) * 4));
@@ -1264,10 +1347,9 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
 }
 
 constexpr int kThreads = 256;
-constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory of one CTA
 constexpr int kVisitThreads = 128;       // threads per CTA of the PRE/POST visit kernels (default)
 constexpr int kBandNodes = 4096;         // residual band of the restriction in shared memory (nodes)
-constexpr int kLowCut = kDW;  // diagonals <= kLowCut of a hierarchy run in one k_low launch
+
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).
 struct Pinned {
@@ -1314,10 +1396,9 @@ struct SolveCtx {
     double* rel;
     CycleParams cp;
     int block;      // threads per CTA of the PRE/POST visit kernels
-    int low_warps;  // items (warps) per CTA of the low-diagonal kernel with one warp per item
-    int low_threads;     // threads per item of the low-diagonal kernel: 32, 64 or 128
+    LowShape low;   // cut and launch shape of the low-diagonal kernel
     const LowDesc* low_desc;
-    const uint2* low_ent;
+    const uint4* low_ent;
     const uint2* low_prog;  // resolved programs of all classes
 };
 
@@ -1341,6 +1422,8 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
     int* slist = (int*)(C.ws + wl.slist[L]);
     int* counter = (int*)(C.ws + wl.counter[L]);
     Segment* dsegs = (Segment*)(C.ws + wl.segs[L]);
+    LowTask* dtasks = (LowTask*)(C.ws + wl.tasks[L]);
+    const int cut = C.low.cut;
     const double es = sizeof(T);
 
     // item types of each group at this stage, and per-sample countdown of open items
@@ -1352,7 +1435,9 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
     for (const ItemType& it : its) nseg_max += 1 + (int64_t)it.pi * it.qi;
     Pinned pin;
     const size_t flag_bytes = sizeof(int) * std::max<int64_t>(pl.stage_nitems[L], 1);
-    if (pin.alloc(64 + 2 * flag_bytes + sizeof(Segment) * std::max<int64_t>(nseg_max, 1)) != MSG_OK) {
+    const size_t seg_bytes = sizeof(Segment) * std::max<int64_t>(nseg_max, 1);
+    const size_t task_bytes = sizeof(LowTask) * (pl.stage_nitems[L] + its.size() + 1);
+    if (pin.alloc(64 + 2 * flag_bytes + seg_bytes + task_bytes) != MSG_OK) {
         set_error("cudaMallocHost failed");
         return MSG_ERR_CUDA;
     }
@@ -1360,6 +1445,8 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
     int* h_flags = (int*)((char*)pin.p + 64);
     int* h_list = (int*)((char*)pin.p + 64 + flag_bytes);
     Segment* h_segs = (Segment*)((char*)pin.p + 64 + 2 * flag_bytes);
+    LowTask* h_tasks = (LowTask*)((char*)pin.p + 64 + 2 * flag_bytes + seg_bytes);
+    int ntasks = 0;
 
     std::vector<std::vector<int>> active(its.size()), fresh(its.size());
     size_t item_nseg = 0;
@@ -1390,7 +1477,15 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         }
         item_nseg = ns;
         if (with_diag) {
-            const int dl = std::min(L, kLowCut);
+            const int dl = std::min(L, cut);
+            // warp tasks of the low-diagonal kernel: up to KW items of one segment (one class) each
+            ntasks = 0;
+            for (size_t k = 0; k < ns; ++k) {
+                const Segment& sgk = h_segs[k];
+                const int cls = low_class(std::min(sgk.pi, dl + 1), std::min(sgk.qi, dl + 1), dl);
+                for (int64_t f = 0; f < sgk.count; f += C.low.items)
+                    h_tasks[ntasks++] = LowTask{(int)k, (int)f, (int)std::min<int64_t>(C.low.items, sgk.count - f), cls};
+            }
             low_bytes = 0;
             for (size_t k = 0; k < its.size(); ++k)
                 for (int pp = 1; pp <= its[k].pi; ++pp)
@@ -1402,7 +1497,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
                         if (dd == dl) low_bytes += n * ((pp < its[k].pi && qq < its[k].qi) ? 3 : 2);
                     }
             low_bytes *= es;
-            for (int d = kLowCut + 1; d <= L; ++d) {
+            for (int d = cut + 1; d <= L; ++d) {
                 dseg0[d] = ns;
                 b = 0;
                 dpre[d] = dpost[d] = 0;
@@ -1427,6 +1522,8 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         MSG_CUDA_TRY(cudaMemcpyAsync(slist, h_list, sizeof(int) * std::max<int64_t>(nl, 1), cudaMemcpyHostToDevice, st));
         MSG_CUDA_TRY(cudaMemcpyAsync(dsegs, h_segs, sizeof(Segment) * std::max<size_t>(ns, 1), cudaMemcpyHostToDevice,
                                      st));
+        if (with_diag && ntasks > 0)
+            MSG_CUDA_TRY(cudaMemcpyAsync(dtasks, h_tasks, sizeof(LowTask) * ntasks, cudaMemcpyHostToDevice, st));
         return MSG_OK;
     };
     auto ctx_of = [&](size_t seg0, size_t n) {
@@ -1550,18 +1647,24 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         DevCtx ic = ctx_of(0, item_nseg);
         bool launch_err = false;
         auto launch_low = [&](int d, int calls) {
+            if (ntasks == 0) return;
+            const LowPlanes& lp = low_tables().planes[d];
+            const int wpb = C.low.warps;
+            const unsigned nb = (unsigned)((ntasks + wpb - 1) / wpb);
+            const size_t es_ = sizeof(T);
+            const int stride = low_stride(lp, C.low.items, es_);
+            const size_t smem = es_ * (size_t)stride * C.low.items * wpb;
+            const T om = (T)C.cp.omega;
             prof_begin(K_LOW, st);
-            if (C.low_threads == 32) {  // one warp per item, low_warps items per CTA
-                const int lw = C.low_warps;
-                const unsigned nb = (unsigned)((nitems + lw - 1) / lw);
-                k_low<T, 32><<<nb, lw * 32, sizeof(T) * kLowSlot * lw, st>>>(
-                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
-            } else if (C.low_threads == 64) {  // one item per CTA
-                k_low<T, 64><<<(unsigned)nitems, 64, sizeof(T) * kLowSlot, st>>>(
-                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
-            } else {
-                k_low<T, 128><<<(unsigned)nitems, 128, sizeof(T) * kLowSlot, st>>>(
-                    ic, nitems, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent, C.low_prog, d, calls, C.cp);
+            switch (C.low.items) {
+            case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
+                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
+            case 2: k_lowv<T, 2><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
+                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
+            case 4: k_lowv<T, 4><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
+                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
+            default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
+                                                             C.low_ent, C.low_prog, lp, stride, calls, om); break;
             }
             prof_end(K_LOW, st, low_bytes, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
@@ -1591,7 +1694,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             prof_end(pre ? K_PRE : K_POST, st, (pre ? dpre[d] : dpost[d]) * es, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
-        if (L <= kLowCut) {
+        if (L <= cut) {
             launch_low(L, 1);
         } else {
             struct Frame { int d, k, zi, phase; };
@@ -1602,7 +1705,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
                 if (f.phase == 0) {
                     launch_half(f.d, 1, f.zi);
                     f.phase = 1;
-                    if (f.d - 1 <= kLowCut) {
+                    if (f.d - 1 <= cut) {
                         launch_low(f.d - 1, C.prm.mu);
                         f.phase = 2;
                     }
@@ -1649,8 +1752,8 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
                   (const double*)(ws + wl.ax64), (const double*)(ws + wl.ay64), nullptr, nullptr,
                   (int*)(ws + wl.nstep), (int*)(ws + wl.cycles_i), (double*)(ws + wl.relres_i),
                   CycleParams{prm.mu, prm.nu1, prm.nu2, prm.omega}, prm.tune_block ? prm.tune_block : kVisitThreads,
-                  prm.tune_low_warps ? prm.tune_low_warps : 2, prm.tune_low_threads ? prm.tune_low_threads : 32,
-                  (const LowDesc*)(ws + wl.low_desc), (const uint2*)(ws + wl.low_ent), (const uint2*)(ws + wl.low_prog)};
+                  low_shape(prm), (const LowDesc*)(ws + wl.low_desc), (const uint4*)(ws + wl.low_ent),
+                  (const uint2*)(ws + wl.low_prog)};
     float* ax32 = mixed ? (float*)(ws + wl.ax32) : nullptr;
     float* ay32 = mixed ? (float*)(ws + wl.ay32) : nullptr;
     C.ax = mixed ? (const T*)ax32 : (const T*)(ws + wl.ax64);
@@ -1676,10 +1779,6 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
         MSG_CHECK_LAUNCH();
     }
-    if (sizeof(T) * kLowSlot * C.low_warps > kSmemMax) {
-        set_error("tune_low_warps items do not fit the shared memory of one CTA");
-        return MSG_ERR_INVALID;
-    }
     {
         // tables of the low-diagonal program: class descriptors, node entries, programs
         const LowTables& lt = low_tables();
@@ -1687,7 +1786,7 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         const std::vector<uint2> rp = low_resolve(prm, desc);
         MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_desc, desc.data(), sizeof(LowDesc) * desc.size(),
                                      cudaMemcpyHostToDevice, st));
-        MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_ent, lt.ent.data(), sizeof(uint2) * lt.ent.size(),
+        MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_ent, lt.ent.data(), sizeof(uint4) * lt.ent.size(),
                                      cudaMemcpyHostToDevice, st));
         MSG_CUDA_TRY(cudaMemcpyAsync(ws + wl.low_prog, rp.data(), sizeof(uint2) * rp.size(),
                                      cudaMemcpyHostToDevice, st));
@@ -1697,12 +1796,10 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     // the residual band: 3 rows of a 2^12-cell-wide grid at most
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * std::max(kBandNodes, 3 * ((1 << 12) + 1)))));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * kLowSlot * C.low_warps)));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * kLowSlot)));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_low<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(T) * kLowSlot)));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     MSG_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- one worker (host thread + stream) per stage

@@ -178,8 +178,9 @@ def test_result_independent_of_batch_mix(msg):
     assert np.array_equal(Qmix[16:26], Qalone)
 
 
-@pytest.mark.parametrize("shape", [dict(tune_low_warps=3), dict(tune_low_threads=64), dict(tune_low_threads=128),
-                                   dict(tune_block=64, tune_low_warps=1), dict(tune_block=256, tune_low_warps=4)])
+@pytest.mark.parametrize("shape", [dict(tune_low_warps=3), dict(tune_low_items=1), dict(tune_low_items=4, tune_low_warps=1),
+                                   dict(tune_low_items=8, tune_low_warps=1), dict(tune_block=64, tune_low_warps=1),
+                                   dict(tune_block=256, tune_low_warps=4)])
 def test_launch_shapes_do_not_change_results(msg, shape):
     """Launch shapes only regroup independent per-node updates: bit-exact results.
     The batch mixes shapes (items of several low-diagonal classes in one CTA)
@@ -190,6 +191,23 @@ def test_launch_shapes_do_not_change_results(msg, shape):
     got = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300, **shape)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("cut", [1, 3, 4])
+def test_low_kernel_cut_changes_rounding_only(msg, cut):
+    """The diagonal up to which the low-diagonal kernel runs the recursion (the rest
+    are separate visit launches) changes only the rounding of the FP32 cycles: every
+    grid still meets eps and the QoIs agree with the default cut and with the oracle
+    to the mixed path's 1e-8."""
+    shapes = SHAPES_SMALL + [(2, 6), (6, 2), (5, 4), (6, 6)]
+    Zs = oracle_fields(shapes, seed=8)
+    ref = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300)
+    got = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300, tune_low_cut=cut)
+    assert np.array_equal(ref[1], got[1]) and (got[1] == 0).all()
+    assert np.all(got[3] <= 1e-10)
+    np.testing.assert_allclose(got[0], ref[0], rtol=1e-8)
+    Qo, _, _ = run_oracle(shapes, Zs, 1e-12, 600)
+    np.testing.assert_allclose(got[0], Qo, rtol=1e-8)
 
 
 # ------------------------------------------------------------------ (a14) --
