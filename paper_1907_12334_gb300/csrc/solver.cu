@@ -450,7 +450,7 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
 constexpr int kLowMax = 5;  // highest diagonal the low kernel can take
 constexpr int kLowGridsMax = (kLowMax + 1) * (kLowMax + 2) / 2;
 constexpr int kLowClassesMax = 91;  // sum over dl = 0..kLowMax of (dl + 1)^2
-constexpr int kLowWarpsMax = 8;     // warps per CTA of the low kernel
+constexpr int kLowWarpsMax = 16;    // warps per CTA of the low kernel
 
 // phase kinds; a resolved program word is {kind | entries << 3, first entry}
 enum LowKind { LK_RED = 0, LK_BLACK, LK_RESID, LK_RESTRICT, LK_PROL, LK_NKIND };
@@ -489,11 +489,13 @@ struct LowPlanes {
 struct LowDesc {
     int dl, pic, qic;
     int prog, nops;                    // resolved program of the class (set per solve)
+    int e0, e1;                        // the class's entries: table[e0 .. e1)
     int cnt[kLowMax + 1][LK_NKIND];    // entries of each (diagonal, kind)
     int off[kLowMax + 1][LK_NKIND];    // first table entry of the phase
 };
 
-// One warp's share of a launch: items first .. first + count - 1 of segment seg.
+// One warp's share of a launch: items first .. first + count - 1 of segment seg
+// (count 0: an idle warp).  The warps of one CTA share the class cls.
 struct LowTask {
     int seg, first, count, cls;
 };
@@ -594,27 +596,36 @@ __device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_
 // Reads the coefficients of the item's grids with d <= dl and the right-hand
 // side of its diagonal-dl grids (combined from the parents' restrictions, or the
 // item's own residual when dl is its top); writes back u of diagonal dl.
+// All warps of a CTA run items of one class: the CTA first copies that class's
+// resolved program (pcap words at most) and table entries (ecap at most) into
+// shared memory, so the chain of phases touches no global memory.
 template <class T, int KW>
-__global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const LowTask* tasks, int ntasks, T* su,
-                                                           const T* sbx, const T* sby, const T* ax, const T* ay,
+__global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const LowTask* tasks, T* su, const T* sbx,
+                                                           const T* sby, const T* ax, const T* ay,
                                                            const LowDesc* descs, const uint4* ent,
-                                                           const uint2* rprog, LowPlanes lp, int stride, int calls,
-                                                           T omega)
+                                                           const uint2* rprog, LowPlanes lp, int stride, int pcap,
+                                                           int ecap, int calls, T omega)
 {
     constexpr int EW = 32 / KW;  // lanes per item
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (gw >= ntasks) return;  // the whole warp
-    const LowTask tk = tasks[gw];
+    uint4* sent = (uint4*)smem_raw;
+    uint2* sprog = (uint2*)(sent + ecap);
+    T* planes = (T*)(sprog + pcap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const LowDesc& D = descs[tasks[(size_t)blockIdx.x * wpb].cls];
+    const int nops = D.nops, nent = D.e1 - D.e0;
+    for (int k = threadIdx.x; k < nops; k += blockDim.x) sprog[k] = rprog[D.prog + k];
+    for (int k = threadIdx.x; k < nent; k += blockDim.x) sent[k] = ent[D.e0 + k];
+    __syncthreads();
+    const LowTask tk = tasks[(size_t)blockIdx.x * wpb + warp];
+    if (tk.count == 0) return;  // the whole warp; no CTA barrier follows
     const int k = lane / EW, el = lane % EW;
     const bool act = k < tk.count;
-    T* u = (T*)smem_raw + ((size_t)warp * KW + k) * stride;
+    T* u = planes + ((size_t)warp * KW + k) * stride;
     T* b = u + lp.nu;
     T* fx = b + lp.nu;
     T* fy = fx + lp.nfx;
     T* r = fy + lp.nfy;
-    const LowDesc& D = descs[tk.cls];
     const int dl = lp.dl;
     if (act) {
         const TaskRef t = resolve_seg(cx, tk.seg, tk.first + k);
@@ -655,17 +666,13 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
         }
     }
     __syncwarp();
-    const uint2* rp = rprog + D.prog;
-    const int nops = D.nops;
     for (int call = 0; call < calls; ++call) {
-        uint2 op = nops > 0 ? rp[0] : make_uint2(0u, 0u);
         for (int o = 0; o < nops; ++o) {
-            const uint2 nxt = o + 1 < nops ? rp[o + 1] : make_uint2(0u, 0u);
+            const uint2 op = sprog[o];
             const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
             if (act)
-                for (int e = el; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, ent[off + e], omega);
+                for (int e = el; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
             __syncwarp();
-            op = nxt;
         }
     }
     if (act) {
@@ -974,6 +981,7 @@ static void low_build_class(int pic, int qic, int dl, const LowPlanes& L, LowDes
     D.dl = dl;
     D.pic = pic;
     D.qic = qic;
+    D.e0 = (int)ent.size();
     auto exists = [&](int p, int q) { return p >= 1 && q >= 1 && p <= pic && q <= qic && p + q - 2 <= dl; };
     auto grid = [&](int p, int q) -> const LowGrid& {
         for (int k = 0; k < L.ngrid; ++k)
@@ -1054,6 +1062,7 @@ static void low_build_class(int pic, int qic, int dl, const LowPlanes& L, LowDes
         }
         D.cnt[d][LK_PROL] = (int)ent.size() - D.off[d][LK_PROL];
     }
+    D.e1 = (int)ent.size();
 }
 
 static const LowTables& low_tables()
@@ -1098,8 +1107,9 @@ static std::vector<int> low_program(int dl, const msg_params& prm)
 }
 
 // Resolved programs of every class for these parameters: each (kind, diagonal)
-// word becomes {kind | entries << 3, first entry} of the class; phases with no
-// entries are dropped, and so is a residual phase whose restriction is empty.
+// word becomes {kind | entries << 3, first entry relative to the class's e0};
+// phases with no entries are dropped, and so is a residual phase whose
+// restriction is empty.
 static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc)
 {
     desc = low_tables().desc;
@@ -1113,7 +1123,7 @@ static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc
             const int kind = w & 7, d = w >> 3, cnt = D.cnt[d][kind];
             if (cnt == 0) continue;
             if (kind == LK_RESID && D.cnt[d][LK_RESTRICT] == 0) continue;
-            rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)D.off[d][kind]));
+            rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)(D.off[d][kind] - D.e0)));
         }
         D.nops = (int)rp.size() - D.prog;
     }
@@ -1126,20 +1136,43 @@ struct LowShape {
     int cut;    // diagonals <= cut of a hierarchy run inside one k_lowv launch
     int items;  // items per warp (KW)
     int warps;  // warps per CTA
-    int stride; // shared-memory values per item
-    size_t smem;  // bytes per CTA
+    int pcap[kLowMax + 1], ecap[kLowMax + 1];  // program words / entries of the largest class of each dl
+    size_t smem[kLowMax + 1];                  // bytes per CTA of a launch at each dl
 };
+static LowShape low_shape_at(const msg_params& prm, int cut, int items, int warps)
+{
+    const size_t es = prm.precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    const LowTables& lt = low_tables();
+    std::vector<LowDesc> desc;
+    low_resolve(prm, desc);
+    LowShape s;
+    s.cut = cut;
+    s.items = items;
+    s.warps = warps;
+    for (int dl = 0; dl <= kLowMax; ++dl) {
+        s.pcap[dl] = s.ecap[dl] = 0;
+        for (const LowDesc& D : desc)
+            if (D.dl == dl) {
+                s.pcap[dl] = std::max(s.pcap[dl], D.nops);
+                s.ecap[dl] = std::max(s.ecap[dl], D.e1 - D.e0);
+            }
+        s.smem[dl] = sizeof(uint4) * s.ecap[dl] + sizeof(uint2) * s.pcap[dl] +
+                     es * (size_t)low_stride(lt.planes[dl], items, es) * items * warps;
+    }
+    return s;
+}
 static LowShape low_shape(const msg_params& prm)
 {
     const bool mixed = prm.precision == MSG_PREC_MIXED;
-    const size_t es = mixed ? sizeof(float) : sizeof(double);
-    LowShape s;
-    s.cut = prm.tune_low_cut ? prm.tune_low_cut : (mixed ? 5 : 4);
-    s.items = prm.tune_low_items ? prm.tune_low_items : (mixed ? 2 : 2);
-    s.warps = prm.tune_low_warps ? prm.tune_low_warps : 2;
-    s.stride = low_stride(low_tables().planes[s.cut], s.items, es);
-    s.smem = es * (size_t)s.stride * s.items * s.warps;
-    return s;
+    const int items = prm.tune_low_items ? prm.tune_low_items : 1;
+    const int warps = prm.tune_low_warps ? prm.tune_low_warps : (mixed ? 8 : 4);
+    if (prm.tune_low_cut) return low_shape_at(prm, prm.tune_low_cut, items, warps);
+    // default: the highest cut (5 mixed, 4 FP64) whose CTA fits the shared memory
+    for (int cut = mixed ? 5 : 4; cut > 1; --cut) {
+        LowShape s = low_shape_at(prm, cut, items, warps);
+        if (s.smem[cut] <= 227 * 1024) return s;
+    }
+    return low_shape_at(prm, 1, items, warps);
 }
 
 struct Plan {
@@ -1184,14 +1217,15 @@ int validate(const int32_t* PQ, int64_t S, const msg_params* prm)
         return MSG_ERR_INVALID;
     }
     if (prm->tune_low_warps < 0 || prm->tune_low_warps > kLowWarpsMax) {
-        set_error("tune_low_warps must be in [0, 8]");
+        set_error("tune_low_warps must be in [0, 16]");
         return MSG_ERR_INVALID;
     }
     if (prm->tune_low_cut < 0 || prm->tune_low_cut > kLowMax) {
         set_error("tune_low_cut must be in [0, 5]");
         return MSG_ERR_INVALID;
     }
-    if (low_shape(*prm).smem > kSmemMax) {
+    const LowShape ls = low_shape(*prm);
+    if (ls.smem[ls.cut] > kSmemMax) {
         set_error("tune_low_warps x tune_low_items items of the low-diagonal kernel do not fit the shared memory of one CTA");
         return MSG_ERR_INVALID;
     }
@@ -1334,7 +1368,7 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
         for (const ItemType& it : pl.stage_items[L]) nseg += 1 + (int64_t)it.pi * it.qi;
         for (const Group& g : pl.stage_groups[L]) scr += g.scr_per_sample * g.count;
         w.segs.push_back(take(sizeof(Segment) * nseg));
-        w.tasks.push_back(take(sizeof(LowTask) * (pl.stage_nitems[L] + pl.stage_items[L].size())));
+        w.tasks.push_back(take(sizeof(LowTask) * (pl.stage_nitems[L] + pl.stage_items[L].size() * kLowWarpsMax)));
         w.slist.push_back(take(sizeof(int) * pl.stage_nitems[L]));
         w.sflag.push_back(take(sizeof(int) * pl.stage_nitems[L]));
         w.counter.push_back(take(sizeof(int) * 4));
@@ -1436,7 +1470,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
     Pinned pin;
     const size_t flag_bytes = sizeof(int) * std::max<int64_t>(pl.stage_nitems[L], 1);
     const size_t seg_bytes = sizeof(Segment) * std::max<int64_t>(nseg_max, 1);
-    const size_t task_bytes = sizeof(LowTask) * (pl.stage_nitems[L] + its.size() + 1);
+    const size_t task_bytes = sizeof(LowTask) * (pl.stage_nitems[L] + its.size() * C.low.warps + 1);
     if (pin.alloc(64 + 2 * flag_bytes + seg_bytes + task_bytes) != MSG_OK) {
         set_error("cudaMallocHost failed");
         return MSG_ERR_CUDA;
@@ -1479,12 +1513,14 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
         if (with_diag) {
             const int dl = std::min(L, cut);
             // warp tasks of the low-diagonal kernel: up to KW items of one segment (one class) each
+            // (the warps of a CTA take tasks of one segment: idle warps pad each segment's last CTA)
             ntasks = 0;
             for (size_t k = 0; k < ns; ++k) {
                 const Segment& sgk = h_segs[k];
                 const int cls = low_class(std::min(sgk.pi, dl + 1), std::min(sgk.qi, dl + 1), dl);
                 for (int64_t f = 0; f < sgk.count; f += C.low.items)
                     h_tasks[ntasks++] = LowTask{(int)k, (int)f, (int)std::min<int64_t>(C.low.items, sgk.count - f), cls};
+                while (ntasks % C.low.warps) h_tasks[ntasks++] = LowTask{(int)k, 0, 0, cls};
             }
             low_bytes = 0;
             for (size_t k = 0; k < its.size(); ++k)
@@ -1650,21 +1686,21 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             if (ntasks == 0) return;
             const LowPlanes& lp = low_tables().planes[d];
             const int wpb = C.low.warps;
-            const unsigned nb = (unsigned)((ntasks + wpb - 1) / wpb);
-            const size_t es_ = sizeof(T);
-            const int stride = low_stride(lp, C.low.items, es_);
-            const size_t smem = es_ * (size_t)stride * C.low.items * wpb;
+            const unsigned nb = (unsigned)(ntasks / wpb);  // tasks are padded to whole CTAs
+            const int stride = low_stride(lp, C.low.items, sizeof(T));
+            const size_t smem = C.low.smem[d];
+            const int pc = C.low.pcap[d], ec = C.low.ecap[d];
             const T om = (T)C.cp.omega;
             prof_begin(K_LOW, st);
             switch (C.low.items) {
-            case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
-                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
-            case 2: k_lowv<T, 2><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
-                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
-            case 4: k_lowv<T, 4><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
-                                                            C.low_ent, C.low_prog, lp, stride, calls, om); break;
-            default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, ntasks, su, sbx, sby, C.ax, C.ay, C.low_desc,
-                                                             C.low_ent, C.low_prog, lp, stride, calls, om); break;
+            case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+                                                            C.low_prog, lp, stride, pc, ec, calls, om); break;
+            case 2: k_lowv<T, 2><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+                                                            C.low_prog, lp, stride, pc, ec, calls, om); break;
+            case 4: k_lowv<T, 4><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+                                                            C.low_prog, lp, stride, pc, ec, calls, om); break;
+            default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+                                                             C.low_prog, lp, stride, pc, ec, calls, om); break;
             }
             prof_end(K_LOW, st, low_bytes, 0.0, d);
             launch_err |= cudaGetLastError() != cudaSuccess;

@@ -30,6 +30,10 @@ static int check_bounds()
             for (int qic = 1; qic <= dl + 1; ++qic) {
                 const LowDesc& D = lt.desc[low_class(pic, qic, dl)];
                 if (D.dl != dl || D.pic != pic || D.qic != qic) { printf("class index\n"); bad++; }
+                for (int d = 0; d <= dl; ++d)
+                    for (int kd = 0; kd < LK_NKIND; ++kd)
+                        if (D.cnt[d][kd] && (D.off[d][kd] < D.e0 || D.off[d][kd] + D.cnt[d][kd] > D.e1)) {
+                            printf("entries outside the class range\n"); bad++; }
                 auto node = [&](uint4 e, bool resid) {
                     int c = e.x & 0xFFFF, uw = e.x >> 16, ue = e.y & 0xFFFF, us = e.y >> 16, un = e.z & 0xFFFF;
                     int xw = e.z >> 16, ys = e.w & 0xFFFF, r = e.w >> 16;
@@ -89,7 +93,7 @@ static int check_bounds()
             for (const LowDesc& D : desc)
                 for (int o = 0; o < D.nops; ++o) {
                     uint2 w = rp[D.prog + o]; int kind = w.x & 7, cnt = w.x >> 3, off = w.y;
-                    if (kind >= LK_NKIND || cnt <= 0 || off < 0 || off + (size_t)cnt > lt.ent.size()) bad++;
+                    if (kind >= LK_NKIND || cnt <= 0 || off < 0 || D.e0 + off + cnt > D.e1) bad++;
                 }
         }
     printf("bounds: %zu table entries, %d out of range\n", lt.ent.size(), bad);
@@ -153,7 +157,7 @@ static int check_program()
                     T* u = buf.data() + (size_t)it * stride; T* b = u + L.nu; T* fx = b + L.nu; T* fy = fx + L.nfx;
                     T* r = fy + L.nfy;
                     for (int k = cnt - 1; k >= 0; --k)  // any order within a phase gives the same values
-                        low_phase(kind, u, b, fx, fy, r, lt.ent[off + k], (T)1.0);
+                        low_phase(kind, u, b, fx, fy, r, lt.ent[D.e0 + off + k], (T)1.0);
                 }
             }
         for (int it = 0; it < KW; ++it) {

@@ -72,9 +72,10 @@ def test_workspace_bytes_host_logic(lib):
                                     ([[3, 3]], {"max_cycles": 0}), ([[3, 3]], {"omega": 0.0}),
                                     ([[3, 3]], {"precision": 7}), ([[3, 3]], {"qoi": 9}),
                                     ([[3, 3]], {"eps": float("nan")}), ([[3, 3]], {"nu1": 65}),
-                                    ([[3, 3]], {"tune_block": 48}), ([[3, 3]], {"tune_low_warps": 9}),
+                                    ([[3, 3]], {"tune_block": 48}), ([[3, 3]], {"tune_low_warps": 17}),
                                     ([[3, 3]], {"tune_low_items": 3}),
-                                    ([[3, 3]], {"tune_low_cut": 6}), ([[3, 3]], {"tune_low_items": 8, "tune_low_warps": 8})])
+                                    ([[3, 3]], {"tune_low_cut": 6}),
+                                    ([[3, 3]], {"tune_low_items": 8, "tune_low_warps": 8, "tune_low_cut": 5})])
 def test_invalid_arguments_rejected_on_host(lib, PQ, kw):
     assert _ws(PQ, **kw) == 0
     assert lib.msg_last_error() != b""
