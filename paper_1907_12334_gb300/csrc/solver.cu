@@ -452,8 +452,9 @@ constexpr int kLowGridsMax = (kLowMax + 1) * (kLowMax + 2) / 2;
 constexpr int kLowClassesMax = 91;  // sum over dl = 0..kLowMax of (dl + 1)^2
 constexpr int kLowWarpsMax = 16;    // warps per CTA of the low kernel
 
-// phase kinds; a resolved program word is {kind | entries << 3, first entry}
-enum LowKind { LK_RED = 0, LK_BLACK, LK_RESID, LK_RESTRICT, LK_PROL, LK_NKIND };
+// phase kinds; a resolved program word is {kind | entries << 3, first entry}.
+// LK_CALL2 stands for the mu recursive calls below diagonal 3, run in registers.
+enum LowKind { LK_RED = 0, LK_BLACK, LK_RESID, LK_RESTRICT, LK_PROL, LK_CALL2, LK_NKIND };
 
 // Class of the triangle below diagonal dl of an item (pic, qic in 1..dl+1).
 __host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
@@ -465,7 +466,7 @@ __host__ __device__ __forceinline__ int low_class(int pic, int qic, int dl)
 // and nj interior rows in the red-black order of the u and b planes (relative
 // to the grid's first slot).  Odd rows hold h + 1 red and h black nodes, even
 // rows h red and h + 1 black, h = (ni - 1) / 2.
-__host__ __device__ __forceinline__ int low_rb(int ni, int nj, int i, int j)
+__host__ __device__ constexpr int low_rb(int ni, int nj, int i, int j)
 {
     const int h = (ni - 1) >> 1;
     if (((i + j) & 1) == 0) return (j - 1) * h + (j >> 1) + ((i - 1) >> 1);
@@ -577,6 +578,199 @@ __host__ __device__ __forceinline__ void low_phase(int kind, T* u, T* b, const T
     else low_prol(u, fx, fy, e, omega);
 }
 
+
+// ------------------------------------------------ diagonals <= 2 in registers --
+//
+// Below diagonal 3 an item has at most six grids and 30 unknowns, and those
+// levels hold most of the phases of a mu-cycle (each visit of diagonal 3 calls
+// mu cycles on them).  One thread runs those calls for its item: u and b of the
+// six grids live in registers (the code below is unrolled at compile time for
+// each possible clipped shape (PIC, QIC) of the triangle, so every index is a
+// constant), the coefficients are read from the item's face planes in shared
+// memory (the six grids are their first 46 values), and the arithmetic is that
+// of the table phases, node for node.  Register slot k holds u-plane slot k + 1.
+namespace r2 {
+__host__ __device__ constexpr int grid(int p, int q)
+{
+    return (p == 1 && q == 1) ? 0 : (p == 1 && q == 2) ? 1 : (p == 2 && q == 1) ? 2 : (p == 1 && q == 3) ? 3
+         : (p == 2 && q == 2) ? 4 : 5;
+}
+__host__ __device__ constexpr int gu(int g) { return g == 0 ? 0 : g == 1 ? 1 : g == 2 ? 4 : g == 3 ? 7 : g == 4 ? 14 : 23; }
+__host__ __device__ constexpr int gx(int g) { return g == 0 ? 0 : g == 1 ? 2 : g == 2 ? 8 : g == 3 ? 12 : g == 4 ? 26 : 38; }
+__host__ __device__ constexpr int gy(int g) { return g == 0 ? 0 : g == 1 ? 2 : g == 2 ? 6 : g == 3 ? 12 : g == 4 ? 20 : 32; }
+// register slot of interior node (i, j) of grid (p, q)
+__host__ __device__ constexpr int at(int p, int q, int i, int j)
+{
+    return gu(grid(p, q)) + low_rb((1 << p) - 1, (1 << q) - 1, i, j);
+}
+constexpr int kN = 30;  // unknowns of the six grids
+}  // namespace r2
+
+template <class T, int PIC, int QIC>
+struct Reg2 {
+    // the coefficients stay in shared memory (re-read at each use: 92 of them would not fit beside u, b)
+    typedef const volatile T* CP;
+    static constexpr bool has(int p, int q) { return p >= 1 && q >= 1 && p <= PIC && q <= QIC && p + q <= 4; }
+
+    // u at node (i, j) of grid (p, q); boundary nodes read the zero slot's value
+    template <int P, int Q>
+    __host__ __device__ static __forceinline__ T get(const T* u, int i, int j)
+    {
+        return (i > 0 && i < (1 << P) && j > 0 && j < (1 << Q)) ? u[r2::at(P, Q, i, j)] : T(0);
+    }
+
+    template <int P, int Q>
+    __host__ __device__ static __forceinline__ void smooth(T* u, const T* b, CP fx, CP fy, int colour)
+    {
+        constexpr int nx = 1 << P, ny = 1 << Q, g = r2::grid(P, Q);
+#pragma unroll
+        for (int j = 1; j < ny; ++j)
+#pragma unroll
+            for (int i = 1; i < nx; ++i) {
+                if (((i + j) & 1) != colour) continue;
+                const int xw = r2::gx(g) + (j - 1) * nx + (i - 1), ys = r2::gy(g) + (i - 1) * ny + (j - 1);
+                const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
+                const T nb = (aw * get<P, Q>(u, i - 1, j) + ae * get<P, Q>(u, i + 1, j)) +
+                             (as * get<P, Q>(u, i, j - 1) + an * get<P, Q>(u, i, j + 1));
+                const int c = r2::at(P, Q, i, j);
+                u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
+            }
+    }
+
+    template <int P, int Q>
+    __host__ __device__ static __forceinline__ T res(const T* u, const T* b, CP fx, CP fy, int i, int j)
+    {
+        constexpr int nx = 1 << P, ny = 1 << Q, g = r2::grid(P, Q);
+        const int xw = r2::gx(g) + (j - 1) * nx + (i - 1), ys = r2::gy(g) + (i - 1) * ny + (j - 1);
+        const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
+        const T Au = (aw + ae + as + an) * get<P, Q>(u, i, j) - (aw * get<P, Q>(u, i - 1, j) + ae * get<P, Q>(u, i + 1, j)) -
+                     (as * get<P, Q>(u, i, j - 1) + an * get<P, Q>(u, i, j + 1));
+        return b[r2::at(P, Q, i, j)] - Au;
+    }
+
+    // Eq. (2.3) into child (P, Q) from its parents (P+1, Q) and (P, Q+1); the child's u restarts at 0
+    template <int P, int Q>
+    __host__ __device__ static __forceinline__ void restrict_to(T* u, T* b, CP fx, CP fy)
+    {
+        constexpr bool hx = has(P + 1, Q), hy = has(P, Q + 1);
+        constexpr int nx = 1 << P, ny = 1 << Q;
+#pragma unroll
+        for (int j = 1; j < ny; ++j)
+#pragma unroll
+            for (int i = 1; i < nx; ++i) {
+                T vx = T(0), vy = T(0);
+                if constexpr (hx)
+                    vx = T(0.25) * (res<P + 1, Q>(u, b, fx, fy, 2 * i - 1, j) + T(2) * res<P + 1, Q>(u, b, fx, fy, 2 * i, j) +
+                                    res<P + 1, Q>(u, b, fx, fy, 2 * i + 1, j));
+                if constexpr (hy)
+                    vy = T(0.25) * (res<P, Q + 1>(u, b, fx, fy, i, 2 * j - 1) + T(2) * res<P, Q + 1>(u, b, fx, fy, i, 2 * j) +
+                                    res<P, Q + 1>(u, b, fx, fy, i, 2 * j + 1));
+                const int c = r2::at(P, Q, i, j);
+                b[c] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+                u[c] = T(0);
+            }
+    }
+
+    // Eq. (2.4)/(2.5) into fine grid (P, Q) from its children (P-1, Q) and (P, Q-1)
+    template <int P, int Q>
+    __host__ __device__ static __forceinline__ void prolong(T* u, CP fx, CP fy, T omega)
+    {
+        constexpr bool hx = P > 1, hy = Q > 1;
+        constexpr int nx = 1 << P, ny = 1 << Q, g = r2::grid(P, Q);
+#pragma unroll
+        for (int j = 1; j < ny; ++j)
+#pragma unroll
+            for (int i = 1; i < nx; ++i) {
+                T vx = T(0), vy = T(0);
+                if constexpr (hx) vx = T(0.5) * (get<P - 1, Q>(u, i >> 1, j) + get<P - 1, Q>(u, (i + 1) >> 1, j));
+                if constexpr (hy) vy = T(0.5) * (get<P, Q - 1>(u, i, j >> 1) + get<P, Q - 1>(u, i, (j + 1) >> 1));
+                T corr;
+                if constexpr (hx && hy) {
+                    const int xw = r2::gx(g) + (j - 1) * nx + (i - 1), ys = r2::gy(g) + (i - 1) * ny + (j - 1);
+                    const T cxv = fx[xw] + fx[xw + 1], cyv = fy[ys] + fy[ys + 1];
+                    const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+                    corr = (x2 * s) * vx + (y2 * s) * vy;
+                } else {
+                    corr = hx ? vx : vy;
+                }
+                u[r2::at(P, Q, i, j)] += omega * corr;  // the children's u are not written here
+            }
+    }
+
+    __host__ __device__ static __forceinline__ void smooth_diag(int d, T* u, const T* b, CP fx, CP fy, int colour)
+    {
+        if (d == 2) {
+            if constexpr (has(1, 3)) smooth<1, 3>(u, b, fx, fy, colour);
+            if constexpr (has(2, 2)) smooth<2, 2>(u, b, fx, fy, colour);
+            if constexpr (has(3, 1)) smooth<3, 1>(u, b, fx, fy, colour);
+        } else {
+            if constexpr (has(1, 2)) smooth<1, 2>(u, b, fx, fy, colour);
+            if constexpr (has(2, 1)) smooth<2, 1>(u, b, fx, fy, colour);
+        }
+    }
+
+    // mu-cycle of Algorithm 1 at diagonal 1 (one visit; diagonal 0 solved exactly once)
+    __host__ __device__ static __forceinline__ void cycle1(T* u, T* b, CP fx, CP fy, int nu1, int nu2, T omega)
+    {
+        for (int s = 0; s < nu1; ++s) { smooth_diag(1, u, b, fx, fy, 0); smooth_diag(1, u, b, fx, fy, 1); }
+        restrict_to<1, 1>(u, b, fx, fy);
+        smooth<1, 1>(u, b, fx, fy, 0);
+        if constexpr (has(1, 2)) prolong<1, 2>(u, fx, fy, omega);
+        if constexpr (has(2, 1)) prolong<2, 1>(u, fx, fy, omega);
+        for (int s = 0; s < nu2; ++s) { smooth_diag(1, u, b, fx, fy, 0); smooth_diag(1, u, b, fx, fy, 1); }
+    }
+
+    // mu-cycle of Algorithm 1 at diagonal 2
+    __host__ __device__ static __forceinline__ void cycle2(T* u, T* b, CP fx, CP fy, int mu, int nu1, int nu2,
+                                                           T omega)
+    {
+        for (int s = 0; s < nu1; ++s) { smooth_diag(2, u, b, fx, fy, 0); smooth_diag(2, u, b, fx, fy, 1); }
+        if constexpr (has(1, 2)) restrict_to<1, 2>(u, b, fx, fy);
+        if constexpr (has(2, 1)) restrict_to<2, 1>(u, b, fx, fy);
+        for (int k = 0; k < mu; ++k) cycle1(u, b, fx, fy, nu1, nu2, omega);
+        if constexpr (has(1, 3)) prolong<1, 3>(u, fx, fy, omega);
+        if constexpr (has(2, 2)) prolong<2, 2>(u, fx, fy, omega);
+        if constexpr (has(3, 1)) prolong<3, 1>(u, fx, fy, omega);
+        for (int s = 0; s < nu2; ++s) { smooth_diag(2, u, b, fx, fy, 0); smooth_diag(2, u, b, fx, fy, 1); }
+    }
+
+    // the mu calls of a diagonal-3 visit: b of the diagonal-2 grids in, their u out (planes
+    // indexed like the kernel's u and b planes, slot 0 the zero)
+    __host__ __device__ static __forceinline__ void run(T* su, const T* sb, CP fx, CP fy, int mu, int nu1,
+                                                        int nu2, T omega)
+    {
+        T u[r2::kN], b[r2::kN];
+#pragma unroll
+        for (int k = 0; k < r2::kN; ++k) {
+            u[k] = T(0);
+            b[k] = T(0);
+        }
+#pragma unroll
+        for (int k = r2::gu(3); k < r2::kN; ++k) b[k] = sb[1 + k];
+        for (int k = 0; k < mu; ++k) cycle2(u, b, fx, fy, mu, nu1, nu2, omega);
+#pragma unroll
+        for (int k = r2::gu(3); k < r2::kN; ++k) su[1 + k] = u[k];
+    }
+};
+
+// Register path of one item for its class's clipped triangle below diagonal 3.
+template <class T>
+__host__ __device__ __forceinline__ void low_call2(int pic, int qic, T* u, const T* b, const T* fx, const T* fy, int mu,
+                                                   int nu1, int nu2, T omega)
+{
+    pic = pic < 3 ? pic : 3;
+    qic = qic < 3 ? qic : 3;
+    switch (pic * 4 + qic) {
+    case 1 * 4 + 3: Reg2<T, 1, 3>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    case 2 * 4 + 2: Reg2<T, 2, 2>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    case 2 * 4 + 3: Reg2<T, 2, 3>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    case 3 * 4 + 1: Reg2<T, 3, 1>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    case 3 * 4 + 2: Reg2<T, 3, 2>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    case 3 * 4 + 3: Reg2<T, 3, 3>::run(u, b, fx, fy, mu, nu1, nu2, omega); break;
+    default: break;  // no item has a smaller triangle below a diagonal-3 visit
+    }
+}
+
 __device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_t local)
 {
     const Segment* sg = &cx.segs[seg];
@@ -604,8 +798,9 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
                                                            const T* sby, const T* ax, const T* ay,
                                                            const LowDesc* descs, const uint4* ent,
                                                            const uint2* rprog, LowPlanes lp, int stride, int pcap,
-                                                           int ecap, int calls, T omega)
+                                                           int ecap, int calls, CycleParams cp)
 {
+    const T omega = (T)cp.omega;
     constexpr int EW = 32 / KW;  // lanes per item
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint4* sent = (uint4*)smem_raw;
@@ -670,8 +865,11 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
         for (int o = 0; o < nops; ++o) {
             const uint2 op = sprog[o];
             const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
-            if (act)
+            if (kind == LK_CALL2) {
+                if (act && el == 0) low_call2(D.pic, D.qic, u, b, fx, fy, cp.mu, cp.nu1, cp.nu2, omega);
+            } else if (act) {
                 for (int e = el; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
+            }
             __syncwarp();
         }
     }
@@ -1087,22 +1285,26 @@ static const LowTables& low_tables()
 // Diagonal 0 is solved exactly (one unknown, u = b / A); its b does not change
 // between the mu visits of one parent visit, so the repeats, which would write
 // the same value, are left out.  The kernel starts every item from u = 0.
-static void low_program_rec(int d, const msg_params& prm, std::vector<int>& prog)
+// With reg2, the mu calls below a diagonal-3 visit are one LK_CALL2 phase (the
+// register path runs them for each item).
+static void low_program_rec(int d, const msg_params& prm, bool reg2, std::vector<int>& prog)
 {
     auto emit = [&](int kind, int dd) { prog.push_back(kind | dd << 3); };
     if (d == 0) { emit(LK_RED, 0); return; }
     for (int s = 0; s < prm.nu1; ++s) { emit(LK_RED, d); emit(LK_BLACK, d); }
     emit(LK_RESID, d);
     emit(LK_RESTRICT, d);
-    for (int k = 0; k < (d == 1 ? 1 : prm.mu); ++k) low_program_rec(d - 1, prm, prog);
+    if (reg2 && d == 3) emit(LK_CALL2, 2);
+    else
+        for (int k = 0; k < (d == 1 ? 1 : prm.mu); ++k) low_program_rec(d - 1, prm, reg2, prog);
     emit(LK_PROL, d);
     for (int s = 0; s < prm.nu2; ++s) { emit(LK_RED, d); emit(LK_BLACK, d); }
 }
 
-static std::vector<int> low_program(int dl, const msg_params& prm)
+static std::vector<int> low_program(int dl, const msg_params& prm, bool reg2)
 {
     std::vector<int> prog;
-    low_program_rec(dl, prm, prog);
+    low_program_rec(dl, prm, reg2, prog);
     return prog;
 }
 
@@ -1110,17 +1312,21 @@ static std::vector<int> low_program(int dl, const msg_params& prm)
 // word becomes {kind | entries << 3, first entry relative to the class's e0};
 // phases with no entries are dropped, and so is a residual phase whose
 // restriction is empty.
-static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc)
+static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc, bool reg2 = true)
 {
     desc = low_tables().desc;
     std::vector<int> words[kLowMax + 1];
-    for (int dl = 0; dl <= kLowMax; ++dl) words[dl] = low_program(dl, prm);
+    for (int dl = 0; dl <= kLowMax; ++dl) words[dl] = low_program(dl, prm, reg2);
     std::vector<uint2> rp;
     for (LowDesc& D : desc) {
         D.prog = (int)rp.size();
         if (D.pic == 0) { D.nops = 0; continue; }
         for (int w : words[D.dl]) {
             const int kind = w & 7, d = w >> 3, cnt = D.cnt[d][kind];
+            if (kind == LK_CALL2) {
+                rp.push_back(make_uint2((uint32_t)LK_CALL2 | 1u << 3, 0u));
+                continue;
+            }
             if (cnt == 0) continue;
             if (kind == LK_RESID && D.cnt[d][LK_RESTRICT] == 0) continue;
             rp.push_back(make_uint2((uint32_t)kind | (uint32_t)cnt << 3, (uint32_t)(D.off[d][kind] - D.e0)));
@@ -1690,7 +1896,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             const int stride = low_stride(lp, C.low.items, sizeof(T));
             const size_t smem = C.low.smem[d];
             const int pc = C.low.pcap[d], ec = C.low.ecap[d];
-            const T om = (T)C.cp.omega;
+            const CycleParams om = C.cp;
             prof_begin(K_LOW, st);
             switch (C.low.items) {
             case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,

@@ -4,7 +4,8 @@
 //     written;
 //  2. each class's resolved program, run on the planes through the kernel's own
 //     per-node functions (their host builds) for several items side by side in
-//     one strided buffer, gives bit for bit the values of a plain recursive
+//     one strided buffer, with table phases throughout and with the register path
+//     below diagonal 3, gives bit for bit the values of a plain recursive
 //     W-cycle of Algorithm 1 (with the same two program simplifications: the
 //     restriction clears the child's correction, and diagonal 0 is solved once
 //     per diagonal-1 visit) run on full node arrays of every grid.
@@ -93,6 +94,7 @@ static int check_bounds()
             for (const LowDesc& D : desc)
                 for (int o = 0; o < D.nops; ++o) {
                     uint2 w = rp[D.prog + o]; int kind = w.x & 7, cnt = w.x >> 3, off = w.y;
+                    if (kind == LK_CALL2) { if (D.dl < 3) bad++; continue; }
                     if (kind >= LK_NKIND || cnt <= 0 || off < 0 || D.e0 + off + cnt > D.e1) bad++;
                 }
         }
@@ -107,6 +109,7 @@ static int check_program()
     std::uniform_real_distribution<float> ud(0.05f, 3.0f), ub(-1.f, 1.f);
     int bad = 0, checked = 0;
     const int KW = 3;  // items side by side in one strided buffer, as a warp holds them
+    for (int reg2 = 0; reg2 <= 1; ++reg2)  // table phases throughout, and the register path below diagonal 3
     for (int mu = 1; mu <= 3; ++mu)
     for (int nu = 1; nu <= 2; ++nu)
     for (int dl = 0; dl <= kLowMax; ++dl)
@@ -116,7 +119,7 @@ static int check_program()
         if (dl == kLowMax && mu == 3) continue;  // keeps the host run short; mu = 3 is covered below kLowMax
         msg_params prm{}; prm.mu = mu; prm.nu1 = nu; prm.nu2 = nu; prm.omega = 1.0;
         std::vector<LowDesc> desc;
-        std::vector<uint2> rp = low_resolve(prm, desc);
+        std::vector<uint2> rp = low_resolve(prm, desc, reg2 != 0);
         const LowDesc& D = desc[low_class(pic, qic, dl)];
         const LowPlanes& L = lt.planes[dl];
         const int stride = low_stride(L, 4, sizeof(T));
@@ -156,6 +159,7 @@ static int check_program()
                 for (int it = 0; it < KW; ++it) {
                     T* u = buf.data() + (size_t)it * stride; T* b = u + L.nu; T* fx = b + L.nu; T* fy = fx + L.nfx;
                     T* r = fy + L.nfy;
+                    if (kind == LK_CALL2) { low_call2(pic, qic, u, b, fx, fy, mu, nu, nu, (T)1.0); continue; }
                     for (int k = cnt - 1; k >= 0; --k)  // any order within a phase gives the same values
                         low_phase(kind, u, b, fx, fy, r, lt.ent[D.e0 + off + k], (T)1.0);
                 }
@@ -214,6 +218,7 @@ static int check_program()
                 const LowGrid& LG = L.g[gi];
                 int p = LG.p, q = LG.q;
                 if (!exists(p, q)) continue;
+                if (reg2 && dl >= 3 && p + q - 2 < 2) continue;  // those live in registers only
                 Grid& gr = G[p][q];
                 for (int j = 1; j < gr.ny; ++j)
                     for (int i = 1; i < gr.nx; ++i) {
