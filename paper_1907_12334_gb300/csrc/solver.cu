@@ -608,8 +608,16 @@ constexpr int kN = 30;  // unknowns of the six grids
 
 template <class T, int PIC, int QIC>
 struct Reg2 {
-    // the coefficients stay in shared memory (re-read at each use: 92 of them would not fit beside u, b)
-    typedef const volatile T* CP;
+    // the coefficients stay in shared memory: every grid operation starts with a compiler
+    // barrier, so they are re-read per operation (92 of them would not fit beside u, b)
+    // while the loads inside one operation can still be issued together
+    typedef const T* CP;
+    __host__ __device__ static __forceinline__ void fence()
+    {
+#ifdef __CUDA_ARCH__
+        asm volatile("" ::: "memory");
+#endif
+    }
     static constexpr bool has(int p, int q) { return p >= 1 && q >= 1 && p <= PIC && q <= QIC && p + q <= 4; }
 
     // u at node (i, j) of grid (p, q); boundary nodes read the zero slot's value
@@ -622,6 +630,7 @@ struct Reg2 {
     template <int P, int Q>
     __host__ __device__ static __forceinline__ void smooth(T* u, const T* b, CP fx, CP fy, int colour)
     {
+        fence();
         constexpr int nx = 1 << P, ny = 1 << Q, g = r2::grid(P, Q);
 #pragma unroll
         for (int j = 1; j < ny; ++j)
@@ -652,6 +661,7 @@ struct Reg2 {
     template <int P, int Q>
     __host__ __device__ static __forceinline__ void restrict_to(T* u, T* b, CP fx, CP fy)
     {
+        fence();
         constexpr bool hx = has(P + 1, Q), hy = has(P, Q + 1);
         constexpr int nx = 1 << P, ny = 1 << Q;
 #pragma unroll
@@ -675,6 +685,7 @@ struct Reg2 {
     template <int P, int Q>
     __host__ __device__ static __forceinline__ void prolong(T* u, CP fx, CP fy, T omega)
     {
+        fence();
         constexpr bool hx = P > 1, hy = Q > 1;
         constexpr int nx = 1 << P, ny = 1 << Q, g = r2::grid(P, Q);
 #pragma unroll
@@ -771,6 +782,24 @@ __host__ __device__ __forceinline__ void low_call2(int pic, int qic, T* u, const
     }
 }
 
+// Four independent entries of one phase (no entry reads what another writes).
+template <class T>
+__device__ __forceinline__ void low_phase4(int kind, T* u, T* b, const T* fx, const T* fy, T* r, uint4 w0, uint4 w1,
+                                           uint4 w2, uint4 w3, T omega)
+{
+    if (kind <= LK_BLACK) {
+        low_smooth(u, b, fx, fy, w0); low_smooth(u, b, fx, fy, w1); low_smooth(u, b, fx, fy, w2); low_smooth(u, b, fx, fy, w3);
+    } else if (kind == LK_RESID) {
+        low_resid(u, b, fx, fy, r, w0); low_resid(u, b, fx, fy, r, w1); low_resid(u, b, fx, fy, r, w2);
+        low_resid(u, b, fx, fy, r, w3);
+    } else if (kind == LK_RESTRICT) {
+        low_restrict(u, b, r, w0); low_restrict(u, b, r, w1); low_restrict(u, b, r, w2); low_restrict(u, b, r, w3);
+    } else {
+        low_prol(u, fx, fy, w0, omega); low_prol(u, fx, fy, w1, omega); low_prol(u, fx, fy, w2, omega);
+        low_prol(u, fx, fy, w3, omega);
+    }
+}
+
 __device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_t local)
 {
     const Segment* sg = &cx.segs[seg];
@@ -834,11 +863,13 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
             const int nx = 1 << p, ny = 1 << q, W = nx + 1;
             const int64_t co = S.node_off + grid_offset(p, q, S.Q);
             const int nxf = (ny - 1) << p;  // x-faces (i+1/2, j), j = 1..ny-1, stored at node (i, j)
+#pragma unroll 4
             for (int v = el; v < nxf; v += EW) {
                 const int i = v & (nx - 1), j = 1 + (v >> p);
                 fx[G.gx + v] = ax[co + j * W + i];
             }
             const int nyf = ny << p;  // y-faces (i, j+1/2), i = 1..nx-1, column by column
+#pragma unroll 4
             for (int v = el; v < nyf; v += EW) {
                 const int i = v & (nx - 1), j = v >> p;
                 if (i == 0) continue;
@@ -868,7 +899,14 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
             if (kind == LK_CALL2) {
                 if (act && el == 0) low_call2(D.pic, D.qic, u, b, fx, fy, cp.mu, cp.nu1, cp.nu2, omega);
             } else if (act) {
-                for (int e = el; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
+                // entries of one phase are independent: four per lane in flight at a time
+                int e = el;
+                for (; e + 3 * EW < cnt; e += 4 * EW) {
+                    const uint4 w0 = sent[off + e], w1 = sent[off + e + EW], w2 = sent[off + e + 2 * EW],
+                                w3 = sent[off + e + 3 * EW];
+                    low_phase4(kind, u, b, fx, fy, r, w0, w1, w2, w3, omega);
+                }
+                for (; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
             }
             __syncwarp();
         }
