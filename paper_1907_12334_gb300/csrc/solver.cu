@@ -474,6 +474,8 @@ __host__ __device__ constexpr int low_rb(int ni, int nj, int i, int j)
 }
 
 // Fixed plane layout of the full triangle below dl (independent of the class).
+// Grids are ordered by diagonal, then p, so the layout of a lower dl is a
+// prefix of each plane of the layout of a higher one.
 struct LowGrid {
     int p, q;
     int gu;  // first slot of the grid in u and b
@@ -587,7 +589,7 @@ __host__ __device__ __forceinline__ void low_phase(int kind, T* u, T* b, const T
 // six grids live in registers (the code below is unrolled at compile time for
 // each possible clipped shape (PIC, QIC) of the triangle, so every index is a
 // constant), the coefficients are read from the item's face planes in shared
-// memory (the six grids are their first 46 values), and the arithmetic is that
+// memory (the six grids lead both face planes), and the arithmetic is that
 // of the table phases, node for node.  Register slot k holds u-plane slot k + 1.
 namespace r2 {
 __host__ __device__ constexpr int grid(int p, int q)
@@ -595,9 +597,15 @@ __host__ __device__ constexpr int grid(int p, int q)
     return (p == 1 && q == 1) ? 0 : (p == 1 && q == 2) ? 1 : (p == 2 && q == 1) ? 2 : (p == 1 && q == 3) ? 3
          : (p == 2 && q == 2) ? 4 : 5;
 }
+// the six grids in the layout's order (diagonal, then p) and their offsets in the
+// planes: u/b slots of interior nodes, and x- and y-faces padded to 4 values
+__host__ __device__ constexpr int gp(int g) { return g == 0 ? 1 : g == 1 ? 1 : g == 2 ? 2 : g == 3 ? 1 : g == 4 ? 2 : 3; }
+__host__ __device__ constexpr int gq(int g) { return g == 0 ? 1 : g == 1 ? 2 : g == 2 ? 1 : g == 3 ? 3 : g == 4 ? 2 : 1; }
+// (written out, not recursive, so that the compiler folds them into constant
+// register indices; the host check compares them with the layout builder's)
 __host__ __device__ constexpr int gu(int g) { return g == 0 ? 0 : g == 1 ? 1 : g == 2 ? 4 : g == 3 ? 7 : g == 4 ? 14 : 23; }
-__host__ __device__ constexpr int gx(int g) { return g == 0 ? 0 : g == 1 ? 2 : g == 2 ? 8 : g == 3 ? 12 : g == 4 ? 26 : 38; }
-__host__ __device__ constexpr int gy(int g) { return g == 0 ? 0 : g == 1 ? 2 : g == 2 ? 6 : g == 3 ? 12 : g == 4 ? 20 : 32; }
+__host__ __device__ constexpr int gx(int g) { return g == 0 ? 0 : g == 1 ? 4 : g == 2 ? 12 : g == 3 ? 16 : g == 4 ? 32 : 44; }
+__host__ __device__ constexpr int gy(int g) { return g == 0 ? 0 : g == 1 ? 4 : g == 2 ? 8 : g == 3 ? 16 : g == 4 ? 24 : 36; }
 // register slot of interior node (i, j) of grid (p, q)
 __host__ __device__ constexpr int at(int p, int q, int i, int j)
 {
@@ -624,7 +632,11 @@ struct Reg2 {
     template <int P, int Q>
     __host__ __device__ static __forceinline__ T get(const T* u, int i, int j)
     {
-        return (i > 0 && i < (1 << P) && j > 0 && j < (1 << Q)) ? u[r2::at(P, Q, i, j)] : T(0);
+        // the index stays inside the array even for boundary nodes (whose value is 0), so that
+        // the compiler can keep the unrolled array in registers
+        const bool in = i > 0 && i < (1 << P) && j > 0 && j < (1 << Q);
+        const T v = u[in ? r2::at(P, Q, i, j) : 0];
+        return in ? v : T(0);
     }
 
     template <int P, int Q>
@@ -782,21 +794,83 @@ __host__ __device__ __forceinline__ void low_call2(int pic, int qic, T* u, const
     }
 }
 
-// Four independent entries of one phase (no entry reads what another writes).
+// Four entries of one phase at a time: no entry of a phase reads what another
+// entry of the same phase writes, so all operands are gathered first (their
+// shared-memory loads in flight together), then computed, then stored.
 template <class T>
-__device__ __forceinline__ void low_phase4(int kind, T* u, T* b, const T* fx, const T* fy, T* r, uint4 w0, uint4 w1,
-                                           uint4 w2, uint4 w3, T omega)
+__device__ __forceinline__ void low_phase4(int kind, T* u, T* b, const T* fx, const T* fy, T* r, const uint4 (&e)[4],
+                                           T omega)
 {
-    if (kind <= LK_BLACK) {
-        low_smooth(u, b, fx, fy, w0); low_smooth(u, b, fx, fy, w1); low_smooth(u, b, fx, fy, w2); low_smooth(u, b, fx, fy, w3);
-    } else if (kind == LK_RESID) {
-        low_resid(u, b, fx, fy, r, w0); low_resid(u, b, fx, fy, r, w1); low_resid(u, b, fx, fy, r, w2);
-        low_resid(u, b, fx, fy, r, w3);
+    if (kind <= LK_RESID) {
+        T aw[4], ae[4], as[4], an[4], uw[4], ue[4], us[4], un[4], bc[4], uc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xw = e[k].z >> 16, ys = e[k].w & 0xFFFF;
+            aw[k] = fx[xw]; ae[k] = fx[xw + 1]; as[k] = fy[ys]; an[k] = fy[ys + 1];
+            uw[k] = u[e[k].x >> 16]; ue[k] = u[e[k].y & 0xFFFF]; us[k] = u[e[k].y >> 16]; un[k] = u[e[k].z & 0xFFFF];
+            bc[k] = b[e[k].x & 0xFFFF];
+            uc[k] = kind == LK_RESID ? u[e[k].x & 0xFFFF] : T(0);
+        }
+        if (kind == LK_RESID) {
+            T rv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T Au = (aw[k] + ae[k] + as[k] + an[k]) * uc[k] - (aw[k] * uw[k] + ae[k] * ue[k]) -
+                             (as[k] * us[k] + an[k] * un[k]);
+                rv[k] = bc[k] - Au;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[e[k].w >> 16] = rv[k];
+        } else {
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T nb = (aw[k] * uw[k] + ae[k] * ue[k]) + (as[k] * us[k] + an[k] * un[k]);
+                v[k] = (bc[k] + nb) * rcp_of(aw[k] + ae[k] + as[k] + an[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
+        }
     } else if (kind == LK_RESTRICT) {
-        low_restrict(u, b, r, w0); low_restrict(u, b, r, w1); low_restrict(u, b, r, w2); low_restrict(u, b, r, w3);
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rx = e[k].x >> 16, ry = e[k].y & 0xFFFF, wy = e[k].y >> 16;
+            const bool hx = e[k].z & 1, hy = e[k].z & 2;
+            // absent parents point at slot 0 with stride 0: the loads are valid and ignored
+            const T x0 = r[hx ? rx - 1 : 0], x1 = r[rx], x2 = r[hx ? rx + 1 : 0];
+            const T y0 = r[hy ? ry - wy : 0], y1 = r[ry], y2 = r[hy ? ry + wy : 0];
+            const T vx = hx ? T(0.25) * (x0 + T(2) * x1 + x2) : T(0);
+            const T vy = hy ? T(0.25) * (y0 + T(2) * y1 + y2) : T(0);
+            v[k] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[e[k].x & 0xFFFF] = v[k];
+            u[e[k].x & 0xFFFF] = T(0);
+        }
     } else {
-        low_prol(u, fx, fy, w0, omega); low_prol(u, fx, fy, w1, omega); low_prol(u, fx, fy, w2, omega);
-        low_prol(u, fx, fy, w3, omega);
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = e[k].x & 0xFFFF, xw = e[k].x >> 16, ys = e[k].y & 0xFFFF;
+            const int cx0 = e[k].y >> 16, cx1 = e[k].z & 0xFFFF, cy0 = e[k].z >> 16, cy1 = e[k].w & 0xFFFF;
+            const bool hx = (e[k].w >> 16) & 1, hy = (e[k].w >> 17) & 1;
+            const T ux0 = u[cx0], ux1 = u[cx1], uy0 = u[cy0], uy1 = u[cy1], uc = u[c];
+            const T f0 = fx[xw], f1 = fx[xw + 1], g0 = fy[ys], g1 = fy[ys + 1];
+            const T vx = hx ? T(0.5) * (ux0 + ux1) : T(0), vy = hy ? T(0.5) * (uy0 + uy1) : T(0);
+            T corr;
+            if (hx && hy) {
+                const T cxv = f0 + f1, cyv = g0 + g1;
+                const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+                corr = (x2 * s) * vx + (y2 * s) * vy;
+            } else {
+                corr = hx ? vx : vy;
+            }
+            v[k] = uc + omega * corr;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
     }
 }
 
@@ -824,7 +898,7 @@ __device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_
 // shared memory, so the chain of phases touches no global memory.
 template <class T, int KW>
 __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const LowTask* tasks, T* su, const T* sbx,
-                                                           const T* sby, const T* ax, const T* ay,
+                                                           const T* sby, const T* img, int64_t istride, int ify,
                                                            const LowDesc* descs, const uint4* ent,
                                                            const uint2* rprog, LowPlanes lp, int stride, int pcap,
                                                            int ecap, int calls, CycleParams cp)
@@ -853,28 +927,26 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
     const int dl = lp.dl;
     if (act) {
         const TaskRef t = resolve_seg(cx, tk.seg, tk.first + k);
-        const SampleInfo& S = cx.samples[t.s];
         const int pi = t.seg->pi, qi = t.seg->qi;
+        // the face planes: 16-byte asynchronous copies of the prefixes of the sample's image
+        {
+            constexpr int V = 16 / sizeof(T);
+            const T* im = img + (int64_t)t.s * istride;
+            const uint32_t dfx = (uint32_t)__cvta_generic_to_shared(fx), dfy = (uint32_t)__cvta_generic_to_shared(fy);
+            for (int c = el; c < lp.nfx / V; c += EW)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfx + 16 * c), "l"(im + c * V) : "memory");
+            for (int c = el; c < lp.nfy / V; c += EW)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfy + 16 * c), "l"(im + ify + c * V)
+                             : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
         for (int v = el; v < lp.nu; v += EW) u[v] = T(0);
         for (int g = 0; g < lp.ngrid; ++g) {
             const LowGrid G = lp.g[g];
             const int p = G.p, q = G.q;
             if (p > D.pic || q > D.qic) continue;
             const int nx = 1 << p, ny = 1 << q, W = nx + 1;
-            const int64_t co = S.node_off + grid_offset(p, q, S.Q);
-            const int nxf = (ny - 1) << p;  // x-faces (i+1/2, j), j = 1..ny-1, stored at node (i, j)
-#pragma unroll 4
-            for (int v = el; v < nxf; v += EW) {
-                const int i = v & (nx - 1), j = 1 + (v >> p);
-                fx[G.gx + v] = ax[co + j * W + i];
-            }
-            const int nyf = ny << p;  // y-faces (i, j+1/2), i = 1..nx-1, column by column
-#pragma unroll 4
-            for (int v = el; v < nyf; v += EW) {
-                const int i = v & (nx - 1), j = v >> p;
-                if (i == 0) continue;
-                fy[G.gy + (i - 1) * ny + j] = ay[co + j * W + i];
-            }
+            const int nxf = (ny - 1) << p;
             if (p + q - 2 == dl) {  // b at the interior nodes
                 const int64_t so = t.scr + grid_offset(p, q, qi);
                 const bool hx = p < pi, hy = q < qi;
@@ -890,6 +962,7 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
                 }
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncwarp();
     for (int call = 0; call < calls; ++call) {
@@ -902,9 +975,8 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
                 // entries of one phase are independent: four per lane in flight at a time
                 int e = el;
                 for (; e + 3 * EW < cnt; e += 4 * EW) {
-                    const uint4 w0 = sent[off + e], w1 = sent[off + e + EW], w2 = sent[off + e + 2 * EW],
-                                w3 = sent[off + e + 3 * EW];
-                    low_phase4(kind, u, b, fx, fy, r, w0, w1, w2, w3, omega);
+                    const uint4 w[4] = {sent[off + e], sent[off + e + EW], sent[off + e + 2 * EW], sent[off + e + 3 * EW]};
+                    low_phase4(kind, u, b, fx, fy, r, w, omega);
                 }
                 for (; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
             }
@@ -975,6 +1047,34 @@ __global__ void k_coeffs(DevCtx cx, const double* Z, int coef, double* ax64, dou
         if (ax32) {
             ax32[off + k] = (float)vx;
             ay32[off + k] = (float)vy;
+        }
+    }
+}
+
+// Face image of each sample for the low-diagonal kernel: the x- and y-faces of
+// its grids below diagonal kLowMax in the kernel's plane layout (x-faces from
+// value 0, y-faces from value ify), built once per solve so that a launch copies
+// them into shared memory in 16-byte pieces instead of gathering them.
+template <class T>
+__global__ void k_lowimg(const SampleInfo* samples, const T* ax, const T* ay, LowPlanes lp, T* img, int64_t istride,
+                         int ify)
+{
+    const SampleInfo& S = samples[blockIdx.x];  // one block per sample
+    T* im = img + (int64_t)blockIdx.x * istride;
+    for (int g = 0; g < lp.ngrid; ++g) {
+        const LowGrid G = lp.g[g];
+        const int p = G.p, q = G.q;
+        if (p > S.P || q > S.Q) continue;
+        const int nx = 1 << p, ny = 1 << q, W = nx + 1;
+        const int64_t co = S.node_off + grid_offset(p, q, S.Q);
+        for (int v = threadIdx.x; v < ((ny - 1) << p); v += blockDim.x) {
+            const int i = v & (nx - 1), j = 1 + (v >> p);
+            im[G.gx + v] = ax[co + j * W + i];
+        }
+        for (int v = threadIdx.x; v < (ny << p); v += blockDim.x) {
+            const int i = v & (nx - 1), j = v >> p;
+            if (i == 0) continue;
+            im[ify + G.gy + (i - 1) * ny + j] = ay[co + j * W + i];
         }
     }
 }
@@ -1165,6 +1265,11 @@ struct ItemType {
 
 // ------------------------------------------------ low-diagonal host tables --
 
+// Face counts are padded to whole 16-byte chunks (4 values) so that every plane
+// and every grid's faces start 16-byte aligned: the face planes are copied into
+// shared memory in 16-byte pieces.
+static int low_pad4(int n) { return (n + 3) & ~3; }
+
 // Fixed plane layout of the full triangle below dl.
 static LowPlanes low_planes(int dl)
 {
@@ -1183,12 +1288,13 @@ static LowPlanes low_planes(int dl)
             G.gx = L.nfx;
             G.gy = L.nfy;
             L.nu += (nx - 1) * (ny - 1);
-            L.nfx += nx * (ny - 1);
-            L.nfy += (nx - 1) * ny;
+            L.nfx += low_pad4(nx * (ny - 1));
+            L.nfy += low_pad4((nx - 1) * ny);
             nr += (nx - 1) * (ny - 1);
         }
         L.nr = std::max(L.nr, nr);
     }
+    L.nu = low_pad4(L.nu);
     return L;
 }
 
@@ -1574,6 +1680,7 @@ struct WsLayout {
     size_t nstep, cycles_i, relres_i;
     size_t u64, ax64, ay64, ax32, ay32;
     size_t low_desc, low_ent, low_prog;  // tables of the low-diagonal program
+    size_t low_img;                      // per-sample face images of the low-diagonal kernel
     // per stage L: segment list, sample list, flags, counter, scratch (su, sbx, sby)
     std::vector<size_t> segs, tasks, slist, sflag, counter, su, sbx, sby;
     size_t total;
@@ -1595,6 +1702,11 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
         w.low_desc = take(sizeof(LowDesc) * kLowClassesMax);
         w.low_ent = take(sizeof(uint4) * low_tables().ent.size());
         w.low_prog = take(sizeof(uint2) * low_resolve(prm, desc).size());
+    }
+    {
+        const LowPlanes& lp = low_tables().planes[kLowMax];
+        const size_t es_img = precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
+        w.low_img = take(es_img * (size_t)pl.S * (lp.nfx + lp.nfy));
     }
     w.nstep = take(sizeof(int) * pl.total_q);
     w.cycles_i = take(sizeof(int) * pl.total_q);
@@ -1935,15 +2047,19 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             const size_t smem = C.low.smem[d];
             const int pc = C.low.pcap[d], ec = C.low.ecap[d];
             const CycleParams om = C.cp;
+            const LowPlanes& lpm = low_tables().planes[kLowMax];
+            const T* img = (const T*)(C.ws + wl.low_img);
+            const int64_t istr = lpm.nfx + lpm.nfy;
+            const int ify = lpm.nfx;
             prof_begin(K_LOW, st);
             switch (C.low.items) {
-            case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+            case 1: k_lowv<T, 1><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, img, istr, ify, C.low_desc, C.low_ent,
                                                             C.low_prog, lp, stride, pc, ec, calls, om); break;
-            case 2: k_lowv<T, 2><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+            case 2: k_lowv<T, 2><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, img, istr, ify, C.low_desc, C.low_ent,
                                                             C.low_prog, lp, stride, pc, ec, calls, om); break;
-            case 4: k_lowv<T, 4><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+            case 4: k_lowv<T, 4><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, img, istr, ify, C.low_desc, C.low_ent,
                                                             C.low_prog, lp, stride, pc, ec, calls, om); break;
-            default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, C.ax, C.ay, C.low_desc, C.low_ent,
+            default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, img, istr, ify, C.low_desc, C.low_ent,
                                                              C.low_prog, lp, stride, pc, ec, calls, om); break;
             }
             prof_end(K_LOW, st, low_bytes, 0.0, d);
@@ -2057,6 +2173,12 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
         k_coeffs<<<(unsigned)nb, kThreads, 0, st>>>(c, Z, prm.coef, (double*)(ws + wl.ax64), (double*)(ws + wl.ay64),
                                                    ax32, ay32);
         prof_end(K_COEFFS, st, nodes * (16.0 + 16.0 + (mixed ? 8.0 : 0.0)), 0.0);
+        MSG_CHECK_LAUNCH();
+        const LowPlanes& lp = low_tables().planes[kLowMax];
+        prof_begin(K_COEFFS, st);
+        k_lowimg<T><<<(unsigned)pl.S, kThreads, 0, st>>>(C.base.samples, C.ax, C.ay, lp, (T*)(ws + wl.low_img),
+                                                          (int64_t)(lp.nfx + lp.nfy), lp.nfx);
+        prof_end(K_COEFFS, st, (double)pl.S * (lp.nfx + lp.nfy) * 2.0 * sizeof(T), 0.0);
         MSG_CHECK_LAUNCH();
     }
     {

@@ -78,13 +78,21 @@ static int check_bounds()
             const LowGrid& G = L.g[g];
             int nx = 1 << G.p, ny = 1 << G.q;
             if (G.gu != nu || G.gx != nfx || G.gy != nfy) { printf("layout\n"); bad++; }
-            nu += (nx - 1) * (ny - 1); nfx += nx * (ny - 1); nfy += (nx - 1) * ny;
+            nu += (nx - 1) * (ny - 1); nfx += low_pad4(nx * (ny - 1)); nfy += low_pad4((nx - 1) * ny);
+            if (g < 6 && (r2::gp(g) != G.p || r2::gq(g) != G.q || r2::gu(g) + 1 != G.gu || r2::gx(g) != G.gx ||
+                          r2::gy(g) != G.gy)) { printf("register-path offsets\n"); bad++; }
+            if (G.gx % 4 || G.gy % 4) { printf("face alignment\n"); bad++; }
             std::vector<int> seen((nx - 1) * (ny - 1), 0);
             for (int j = 1; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) seen[low_rb(nx - 1, ny - 1, i, j)]++;
             for (int v : seen) if (v != 1) { printf("rb order\n"); bad++; break; }
         }
-        if (nu != L.nu || nfx != L.nfx || nfy != L.nfy) { printf("plane sizes\n"); bad++; }
+        if (low_pad4(nu) != L.nu || nfx != L.nfx || nfy != L.nfy) { printf("plane sizes\n"); bad++; }
+        if (dl > 0) {  // prefix property: the lower layout's grids keep their offsets
+            const LowPlanes& Lm = lt.planes[dl - 1];
+            for (int g = 0; g < Lm.ngrid; ++g)
+                if (Lm.g[g].gu != L.g[g].gu || Lm.g[g].gx != L.g[g].gx || Lm.g[g].gy != L.g[g].gy) { printf("prefix\n"); bad++; }
+        }
     }
     for (int mu = 1; mu <= 3; ++mu)
         for (int nu = 0; nu <= 3; ++nu) {
