@@ -933,12 +933,19 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
             constexpr int V = 16 / sizeof(T);
             const T* im = img + (int64_t)t.s * istride;
             const uint32_t dfx = (uint32_t)__cvta_generic_to_shared(fx), dfy = (uint32_t)__cvta_generic_to_shared(fy);
-            for (int c = el; c < lp.nfx / V; c += EW)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfx + 16 * c), "l"(im + c * V) : "memory");
-            for (int c = el; c < lp.nfy / V; c += EW)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfy + 16 * c), "l"(im + ify + c * V)
-                             : "memory");
-            asm volatile("cp.async.commit_group;" ::: "memory");
+            const bool aligned = ((dfx | dfy) & 15u) == 0 && (((uintptr_t)im | (uintptr_t)(im + ify)) & 15u) == 0;
+            if (aligned) {
+                for (int c = el; c < lp.nfx / V; c += EW)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfx + 16 * c), "l"(im + c * V)
+                                 : "memory");
+                for (int c = el; c < lp.nfy / V; c += EW)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dfy + 16 * c), "l"(im + ify + c * V)
+                                 : "memory");
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            } else {  // not reached with the host's layout; plain copies keep every access legal
+                for (int v = el; v < lp.nfx; v += EW) fx[v] = im[v];
+                for (int v = el; v < lp.nfy; v += EW) fy[v] = im[ify + v];
+            }
         }
         for (int v = el; v < lp.nu; v += EW) u[v] = T(0);
         for (int g = 0; g < lp.ngrid; ++g) {
@@ -1506,6 +1513,7 @@ static LowShape low_shape_at(const msg_params& prm, int cut, int items, int warp
                 s.pcap[dl] = std::max(s.pcap[dl], D.nops);
                 s.ecap[dl] = std::max(s.ecap[dl], D.e1 - D.e0);
             }
+        s.pcap[dl] = (s.pcap[dl] + 1) & ~1;  // whole 16-byte chunks: the planes after it start 16-byte aligned
         s.smem[dl] = sizeof(uint4) * s.ecap[dl] + sizeof(uint2) * s.pcap[dl] +
                      es * (size_t)low_stride(lt.planes[dl], items, es) * items * warps;
     }

@@ -106,6 +106,33 @@ static int check_bounds()
                     if (kind >= LK_NKIND || cnt <= 0 || off < 0 || D.e0 + off + cnt > D.e1) bad++;
                 }
         }
+    // shared-memory layout of a launch: entries, program, then the items' planes; the
+    // face planes of every item must start 16-byte aligned (they are filled by 16-byte copies)
+    for (int prec = 0; prec <= 1; ++prec)
+        for (int mu = 1; mu <= 3; ++mu)
+            for (int nu = 1; nu <= 3; ++nu) {
+                msg_params prm{}; prm.mu = mu; prm.nu1 = nu; prm.nu2 = nu; prm.precision = prec;
+                const size_t es = prec == MSG_PREC_MIXED ? 4 : 8;
+                for (int kw : {1, 2, 4, 8})
+                    for (int wpb : {1, 3, 8, 16}) {
+                        const LowShape sh = low_shape_at(prm, kLowMax, kw, wpb);
+                        for (int dl = 0; dl <= kLowMax; ++dl) {
+                            const LowPlanes& L = lt.planes[dl];
+                            const int stride = low_stride(L, kw, es);
+                            const size_t base = 16 * (size_t)sh.ecap[dl] + 8 * (size_t)sh.pcap[dl];
+                            for (int w = 0; w < wpb; ++w)
+                                for (int k = 0; k < kw; ++k) {
+                                    const size_t u0 = base + es * (size_t)(w * kw + k) * stride;
+                                    const size_t fx0 = u0 + es * 2 * L.nu, fy0 = fx0 + es * L.nfx;
+                                    if (fx0 % 16 || fy0 % 16 || base % 16) { if (bad < 20) printf("smem alignment\n"); bad++; }
+                                }
+                            if (sh.smem[dl] != base + es * (size_t)stride * kw * wpb) { printf("smem size\n"); bad++; }
+                            if ((L.nfx * es) % 16 || (L.nfy * es) % 16) { printf("plane size\n"); bad++; }
+                        }
+                        const LowPlanes& L5 = lt.planes[kLowMax];
+                        if (((L5.nfx + L5.nfy) * es) % 16 || (L5.nfx * es) % 16) { printf("image stride\n"); bad++; }
+                    }
+            }
     printf("bounds: %zu table entries, %d out of range\n", lt.ent.size(), bad);
     return bad;
 }
