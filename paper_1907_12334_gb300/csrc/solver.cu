@@ -513,71 +513,100 @@ struct LowTask {
 //       fine node c; correction 1/2 (u[cx0] + u[cx1]) from the x-child (the two
 //       coincide at even i), likewise from the y-child.
 
+// Four entries of one phase at a time: no entry of a phase reads what another
+// entry of the same phase writes, so all operands are gathered first (their
+// shared-memory loads in flight together), then computed, then stored.
 template <class T>
-__host__ __device__ __forceinline__ void low_smooth(T* u, const T* b, const T* fx, const T* fy, uint4 e)
+__host__ __device__ __forceinline__ void low_phase4(int kind, T* u, T* b, const T* fx, const T* fy, T* r,
+                                                    const uint4 (&e)[4], T omega)
 {
-    const int c = e.x & 0xFFFF, uw = e.x >> 16, ue = e.y & 0xFFFF, us = e.y >> 16, un = e.z & 0xFFFF;
-    const int xw = e.z >> 16, ys = e.w & 0xFFFF;
-    const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
-    const T nb = (aw * u[uw] + ae * u[ue]) + (as * u[us] + an * u[un]);
-    u[c] = (b[c] + nb) * rcp_of(aw + ae + as + an);
-}
-
-template <class T>
-__host__ __device__ __forceinline__ void low_resid(const T* u, const T* b, const T* fx, const T* fy, T* r, uint4 e)
-{
-    const int c = e.x & 0xFFFF, uw = e.x >> 16, ue = e.y & 0xFFFF, us = e.y >> 16, un = e.z & 0xFFFF;
-    const int xw = e.z >> 16, ys = e.w & 0xFFFF;
-    const T aw = fx[xw], ae = fx[xw + 1], as = fy[ys], an = fy[ys + 1];
-    const T Au = (aw + ae + as + an) * u[c] - (aw * u[uw] + ae * u[ue]) - (as * u[us] + an * u[un]);
-    r[e.w >> 16] = b[c] - Au;
-}
-
-// Eq. (2.3) for one child node: b = R_x r of the x-parent and/or R_y r of the
-// y-parent, averaged when it has both; the child's correction restarts from 0
-// (the recursion's first visit of the child follows every restriction).
-template <class T>
-__host__ __device__ __forceinline__ void low_restrict(T* u, T* b, const T* r, uint4 e)
-{
-    const int c = e.x & 0xFFFF, rx = e.x >> 16, ry = e.y & 0xFFFF, wy = e.y >> 16;
-    const bool hx = e.z & 1, hy = e.z & 2;
-    T vx = T(0), vy = T(0);
-    if (hx) vx = T(0.25) * (r[rx - 1] + T(2) * r[rx] + r[rx + 1]);
-    if (hy) vy = T(0.25) * (r[ry - wy] + T(2) * r[ry] + r[ry + wy]);
-    b[c] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
-    u[c] = T(0);
-}
-
-// Eq. (2.4) with linear P and the kappa weights of Eq. (2.5).
-template <class T>
-__host__ __device__ __forceinline__ void low_prol(T* u, const T* fx, const T* fy, uint4 e, T omega)
-{
-    const int c = e.x & 0xFFFF, xw = e.x >> 16, ys = e.y & 0xFFFF;
-    const int cx0 = e.y >> 16, cx1 = e.z & 0xFFFF, cy0 = e.z >> 16, cy1 = e.w & 0xFFFF;
-    const bool hx = (e.w >> 16) & 1, hy = (e.w >> 17) & 1;
-    T vx = T(0), vy = T(0);
-    if (hx) vx = T(0.5) * (u[cx0] + u[cx1]);
-    if (hy) vy = T(0.5) * (u[cy0] + u[cy1]);
-    T corr;
-    if (hx && hy) {
-        const T cxv = fx[xw] + fx[xw + 1], cyv = fy[ys] + fy[ys + 1];
-        const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
-        corr = (x2 * s) * vx + (y2 * s) * vy;
+    if (kind <= LK_RESID) {
+        // red-black Gauss-Seidel update of one colour, or the residual b - A u
+        T aw[4], ae[4], as[4], an[4], uw[4], ue[4], us[4], un[4], bc[4], uc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xw = e[k].z >> 16, ys = e[k].w & 0xFFFF;
+            aw[k] = fx[xw]; ae[k] = fx[xw + 1]; as[k] = fy[ys]; an[k] = fy[ys + 1];
+            uw[k] = u[e[k].x >> 16]; ue[k] = u[e[k].y & 0xFFFF]; us[k] = u[e[k].y >> 16]; un[k] = u[e[k].z & 0xFFFF];
+            bc[k] = b[e[k].x & 0xFFFF];
+            uc[k] = kind == LK_RESID ? u[e[k].x & 0xFFFF] : T(0);
+        }
+        if (kind == LK_RESID) {
+            T rv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T Au = (aw[k] + ae[k] + as[k] + an[k]) * uc[k] - (aw[k] * uw[k] + ae[k] * ue[k]) -
+                             (as[k] * us[k] + an[k] * un[k]);
+                rv[k] = bc[k] - Au;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[e[k].w >> 16] = rv[k];
+        } else {
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T nb = (aw[k] * uw[k] + ae[k] * ue[k]) + (as[k] * us[k] + an[k] * un[k]);
+                v[k] = (bc[k] + nb) * rcp_of(aw[k] + ae[k] + as[k] + an[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
+        }
+    } else if (kind == LK_RESTRICT) {
+        // Eq. (2.3) for one child node: b = R_x r of the x-parent and/or R_y r of the
+        // y-parent, averaged when it has both; the child's correction restarts from 0
+        // (the recursion's first visit of the child follows every restriction)
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rx = e[k].x >> 16, ry = e[k].y & 0xFFFF, wy = e[k].y >> 16;
+            const bool hx = e[k].z & 1, hy = e[k].z & 2;
+            // absent parents point at slot 0 with stride 0: the loads are valid and ignored
+            const T x0 = r[hx ? rx - 1 : 0], x1 = r[rx], x2 = r[hx ? rx + 1 : 0];
+            const T y0 = r[hy ? ry - wy : 0], y1 = r[ry], y2 = r[hy ? ry + wy : 0];
+            const T vx = hx ? T(0.25) * (x0 + T(2) * x1 + x2) : T(0);
+            const T vy = hy ? T(0.25) * (y0 + T(2) * y1 + y2) : T(0);
+            v[k] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[e[k].x & 0xFFFF] = v[k];
+            u[e[k].x & 0xFFFF] = T(0);
+        }
     } else {
-        corr = hx ? vx : vy;
+        // Eq. (2.4) with linear P and the kappa weights of Eq. (2.5)
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = e[k].x & 0xFFFF, xw = e[k].x >> 16, ys = e[k].y & 0xFFFF;
+            const int cx0 = e[k].y >> 16, cx1 = e[k].z & 0xFFFF, cy0 = e[k].z >> 16, cy1 = e[k].w & 0xFFFF;
+            const bool hx = (e[k].w >> 16) & 1, hy = (e[k].w >> 17) & 1;
+            const T ux0 = u[cx0], ux1 = u[cx1], uy0 = u[cy0], uy1 = u[cy1], uc = u[c];
+            const T f0 = fx[xw], f1 = fx[xw + 1], g0 = fy[ys], g1 = fy[ys + 1];
+            const T vx = hx ? T(0.5) * (ux0 + ux1) : T(0), vy = hy ? T(0.5) * (uy0 + uy1) : T(0);
+            T corr;
+            if (hx && hy) {
+                const T cxv = f0 + f1, cyv = g0 + g1;
+                const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
+                corr = (x2 * s) * vx + (y2 * s) * vy;
+            } else {
+                corr = hx ? vx : vy;
+            }
+            v[k] = uc + omega * corr;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
     }
-    u[c] += omega * corr;
 }
 
-// One phase of the program for one item (the lane's share of its entries).
+// One entry of a phase: the four-entry path with the entry repeated (the same
+// value is written four times), so every node of every launch shape goes
+// through one arithmetic definition.
 template <class T>
 __host__ __device__ __forceinline__ void low_phase(int kind, T* u, T* b, const T* fx, const T* fy, T* r, uint4 e,
                                                    T omega)
 {
-    if (kind <= LK_BLACK) low_smooth(u, b, fx, fy, e);
-    else if (kind == LK_RESID) low_resid(u, b, fx, fy, r, e);
-    else if (kind == LK_RESTRICT) low_restrict(u, b, r, e);
-    else low_prol(u, fx, fy, e, omega);
+    const uint4 w[4] = {e, e, e, e};
+    low_phase4(kind, u, b, fx, fy, r, w, omega);
 }
 
 
@@ -794,86 +823,6 @@ __host__ __device__ __forceinline__ void low_call2(int pic, int qic, T* u, const
     }
 }
 
-// Four entries of one phase at a time: no entry of a phase reads what another
-// entry of the same phase writes, so all operands are gathered first (their
-// shared-memory loads in flight together), then computed, then stored.
-template <class T>
-__device__ __forceinline__ void low_phase4(int kind, T* u, T* b, const T* fx, const T* fy, T* r, const uint4 (&e)[4],
-                                           T omega)
-{
-    if (kind <= LK_RESID) {
-        T aw[4], ae[4], as[4], an[4], uw[4], ue[4], us[4], un[4], bc[4], uc[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int xw = e[k].z >> 16, ys = e[k].w & 0xFFFF;
-            aw[k] = fx[xw]; ae[k] = fx[xw + 1]; as[k] = fy[ys]; an[k] = fy[ys + 1];
-            uw[k] = u[e[k].x >> 16]; ue[k] = u[e[k].y & 0xFFFF]; us[k] = u[e[k].y >> 16]; un[k] = u[e[k].z & 0xFFFF];
-            bc[k] = b[e[k].x & 0xFFFF];
-            uc[k] = kind == LK_RESID ? u[e[k].x & 0xFFFF] : T(0);
-        }
-        if (kind == LK_RESID) {
-            T rv[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const T Au = (aw[k] + ae[k] + as[k] + an[k]) * uc[k] - (aw[k] * uw[k] + ae[k] * ue[k]) -
-                             (as[k] * us[k] + an[k] * un[k]);
-                rv[k] = bc[k] - Au;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) r[e[k].w >> 16] = rv[k];
-        } else {
-            T v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const T nb = (aw[k] * uw[k] + ae[k] * ue[k]) + (as[k] * us[k] + an[k] * un[k]);
-                v[k] = (bc[k] + nb) * rcp_of(aw[k] + ae[k] + as[k] + an[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
-        }
-    } else if (kind == LK_RESTRICT) {
-        T v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int rx = e[k].x >> 16, ry = e[k].y & 0xFFFF, wy = e[k].y >> 16;
-            const bool hx = e[k].z & 1, hy = e[k].z & 2;
-            // absent parents point at slot 0 with stride 0: the loads are valid and ignored
-            const T x0 = r[hx ? rx - 1 : 0], x1 = r[rx], x2 = r[hx ? rx + 1 : 0];
-            const T y0 = r[hy ? ry - wy : 0], y1 = r[ry], y2 = r[hy ? ry + wy : 0];
-            const T vx = hx ? T(0.25) * (x0 + T(2) * x1 + x2) : T(0);
-            const T vy = hy ? T(0.25) * (y0 + T(2) * y1 + y2) : T(0);
-            v[k] = (hx && hy) ? T(0.5) * vx + T(0.5) * vy : (hx ? vx : vy);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            b[e[k].x & 0xFFFF] = v[k];
-            u[e[k].x & 0xFFFF] = T(0);
-        }
-    } else {
-        T v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = e[k].x & 0xFFFF, xw = e[k].x >> 16, ys = e[k].y & 0xFFFF;
-            const int cx0 = e[k].y >> 16, cx1 = e[k].z & 0xFFFF, cy0 = e[k].z >> 16, cy1 = e[k].w & 0xFFFF;
-            const bool hx = (e[k].w >> 16) & 1, hy = (e[k].w >> 17) & 1;
-            const T ux0 = u[cx0], ux1 = u[cx1], uy0 = u[cy0], uy1 = u[cy1], uc = u[c];
-            const T f0 = fx[xw], f1 = fx[xw + 1], g0 = fy[ys], g1 = fy[ys + 1];
-            const T vx = hx ? T(0.5) * (ux0 + ux1) : T(0), vy = hy ? T(0.5) * (uy0 + uy1) : T(0);
-            T corr;
-            if (hx && hy) {
-                const T cxv = f0 + f1, cyv = g0 + g1;
-                const T x2 = cxv * cxv, y2 = cyv * cyv, s = rcp_of(x2 + y2);
-                corr = (x2 * s) * vx + (y2 * s) * vy;
-            } else {
-                corr = hx ? vx : vy;
-            }
-            v[k] = uc + omega * corr;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) u[e[k].x & 0xFFFF] = v[k];
-    }
-}
-
 __device__ __forceinline__ TaskRef resolve_seg(const DevCtx& cx, int seg, int64_t local)
 {
     const Segment* sg = &cx.segs[seg];
@@ -980,12 +929,15 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
                 if (act && el == 0) low_call2(D.pic, D.qic, u, b, fx, fy, cp.mu, cp.nu1, cp.nu2, omega);
             } else if (act) {
                 // entries of one phase are independent: four per lane in flight at a time
-                int e = el;
-                for (; e + 3 * EW < cnt; e += 4 * EW) {
-                    const uint4 w[4] = {sent[off + e], sent[off + e + EW], sent[off + e + 2 * EW], sent[off + e + 3 * EW]};
+                // (a lane's last group repeats its first entry where it has fewer than four)
+                for (int e = el; e < cnt; e += 4 * EW) {
+                    uint4 w[4];
+                    w[0] = sent[off + e];
+                    w[1] = e + EW < cnt ? sent[off + e + EW] : w[0];
+                    w[2] = e + 2 * EW < cnt ? sent[off + e + 2 * EW] : w[0];
+                    w[3] = e + 3 * EW < cnt ? sent[off + e + 3 * EW] : w[0];
                     low_phase4(kind, u, b, fx, fy, r, w, omega);
                 }
-                for (; e < cnt; e += EW) low_phase(kind, u, b, fx, fy, r, sent[off + e], omega);
             }
             __syncwarp();
         }
