@@ -79,7 +79,7 @@ typedef struct {
     int32_t tune_block; /* launch shape: threads per CTA of the visit kernels on mid-size grids (0: 128; multiple of 32; small grids use fewer, grids of 2^12+ cells twice as many) */
     int32_t tune_low_warps; /* launch shape: warps per CTA of the low-diagonal kernel (0: default; 1..16) */
     int32_t tune_low_items; /* launch shape: items one warp of that kernel runs in lockstep: 1, 2, 4 or 8 (0: default) */
-    int32_t tune_low_cut;   /* schedule: the highest diagonal of each hierarchy run inside the low-diagonal kernel (0: default, 5 for MSG_PREC_MIXED and 4 for MSG_PREC_FP64; 1..5); the visits above it are separate launches.  Launch shapes never change results; the cut changes only the rounding of the inner cycles */
+    int32_t tune_low_cut;   /* schedule: the highest diagonal of each hierarchy run inside the low-diagonal kernel (0: default 4, lower when a long mu/nu program does not fit; 1..5); the visits above it are separate launches.  Launch shapes never change results; the cut changes only the rounding of the inner cycles */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */
