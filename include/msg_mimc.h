@@ -16,9 +16,12 @@
  *     never frees them and keeps no reference after the call returns;
  *   - pointers marked [host] are host memory read during the call only;
  *   - work is enqueued on `stream` (a cudaStream_t passed as void*, NULL for
- *     the legacy default stream); results are valid once the stream is
- *     synchronised.  msg_solve_batch additionally synchronises `stream` while
- *     it runs (it reads per-step convergence counts on the host);
+ *     the legacy default stream) and the call returns without waiting for it;
+ *     results are valid once the stream is synchronised.  Host arrays are read
+ *     before the call returns (their contents go through the library's own
+ *     pinned staging).  Exceptions: msg_solve_batch synchronises `stream` while
+ *     it runs (its schedule reads per-step convergence counts on the host), and
+ *     mimc_differences_noalloc returns after its work has finished;
  *   - the return value is MSG_OK or an error code; on error
  *     msg_last_error() returns a description (thread-local string);
  *   - no entry point traps or aborts; per-sample numerical failures are
@@ -40,6 +43,7 @@ extern "C" {
 #define MSG_ERR_WORKSPACE 2   /* workspace smaller than msg_workspace_bytes() */
 #define MSG_ERR_CUDA 3        /* a CUDA runtime call failed */
 #define MSG_ERR_UNSUPPORTED 4 /* option not built or not supported on this device */
+#define MSG_ERR_TIMEOUT 5     /* a bounded wait inside a library kernel ran out (see msg_device_status) */
 
 /* per-sample status bits written by msg_solve_batch */
 #define MSG_SAMPLE_NOT_CONVERGED 1 /* some grid hit max_cycles before eps */
@@ -210,6 +214,14 @@ int32_t msg_profile_read(int32_t kernel_class, int64_t* launches, double* total_
 /* LOW: the diagonal the low program starts from); profile with n = 1 to     */
 /* time every launch.                                                        */
 int32_t msg_profile_read_level(int32_t kernel_class, int32_t level, int64_t* timed, double* total_ms, double* bytes);
+
+/* Deferred kernel status (no counterpart in the paper).  Kernels with bounded */
+/* pipeline waits (the tensor-core KL contraction) do not stop the stream to   */
+/* report: a wait that runs out records it on the device and that kernel      */
+/* leaves its output unwritten.  msg_device_status synchronises the current    */
+/* device and returns MSG_ERR_TIMEOUT if any such wait ran out since the       */
+/* previous call (the record is then cleared), else MSG_OK.                    */
+int32_t msg_device_status(void);
 
 /* Description of the last error on this thread ("" if none). */
 const char* msg_last_error(void);

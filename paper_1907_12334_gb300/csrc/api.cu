@@ -1,4 +1,5 @@
 // api.cu -- error state, version, launch counting and profiling of the C ABI.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -51,6 +52,66 @@ bool sample_one_in(int n)
     return t_rng % (uint64_t)n == 0;
 }
 }  // namespace
+
+namespace {
+struct StagingSlot {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;
+    int dev = -1;
+    bool pending = false;  // an event was recorded and may not have completed
+    bool held = false;     // handed out, not yet released
+};
+std::mutex g_staging_mu;
+std::vector<StagingSlot> g_staging;
+}  // namespace
+
+int staging_acquire(size_t bytes, void** ptr, int* token)
+{
+    int dev = 0;
+    MSG_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_staging_mu);
+    for (size_t k = 0; k < g_staging.size(); ++k) {
+        StagingSlot& s = g_staging[k];
+        if (s.held || s.bytes < bytes) continue;
+        if (s.pending) {
+            if (cudaEventQuery(s.ev) != cudaSuccess) continue;  // still being read by an earlier copy
+            s.pending = false;
+        }
+        s.held = true;
+        *ptr = s.p;
+        *token = (int)k;
+        return MSG_OK;
+    }
+    StagingSlot s;
+    s.bytes = std::max<size_t>(bytes, 4096);
+    MSG_CUDA_TRY(cudaHostAlloc(&s.p, s.bytes, cudaHostAllocPortable));
+    s.held = true;
+    g_staging.push_back(s);
+    *ptr = s.p;
+    *token = (int)g_staging.size() - 1;
+    return MSG_OK;
+}
+
+int staging_release(int token, cudaStream_t st)
+{
+    int dev = 0;
+    MSG_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_staging_mu);
+    StagingSlot& s = g_staging[token];
+    if (s.ev && s.dev != dev) {  // events belong to a device
+        cudaEventDestroy(s.ev);
+        s.ev = nullptr;
+    }
+    if (!s.ev) {
+        MSG_CUDA_TRY(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+        s.dev = dev;
+    }
+    MSG_CUDA_TRY(cudaEventRecord(s.ev, st));
+    s.pending = true;
+    s.held = false;
+    return MSG_OK;
+}
 
 void set_error(const std::string& what) { g_last_error = what; }
 void clear_error() { g_last_error.clear(); }

@@ -32,6 +32,14 @@ void clear_error();
         }                                                                                         \
     } while (0)
 
+// Pinned host staging for the host-side tables an entry point uploads, so that
+// the upload is a true asynchronous copy and the call returns without waiting
+// for the stream.  staging_acquire hands out a slot of at least `bytes`;
+// staging_release records an event on `st` after the copies from the slot were
+// enqueued, and the slot is handed out again only once that event has completed.
+int staging_acquire(size_t bytes, void** ptr, int* token);
+int staging_release(int token, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Hierarchy layout.
 //

@@ -38,7 +38,7 @@ constexpr long long kSpinLimit = 1ll << 22;             // bounded mbarrier wait
 
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-__device__ int g_tc_error;  // set by a kernel whose mbarrier wait ran out
+__device__ int g_tc_error;  // set by a kernel whose mbarrier wait ran out (sticky until msg_device_status)
 
 // Byte offset of element (r, k), 0 <= k < 64, in a K-major tile with the
 // 128-byte swizzle: 8-row atoms of 1024 bytes, 16-byte chunk c of row rr
@@ -296,8 +296,6 @@ int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, const double
     const __nv_bfloat16* Blo = (const __nv_bfloat16*)(b + L.lo);
     const double* sl = (const double*)(b + L.sl);
     dim3 grid((unsigned)(L.Np / kTN), (unsigned)((S + kTM - 1) / kTM));
-    int zero = 0;
-    MSG_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
     prof_begin(K_KL, st);
     if (z_fp32) {
         MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
@@ -309,14 +307,22 @@ int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, const double
     // algorithmic work: 3 split products of 2 npts M S flops; bytes: Phi parts, xi, Z
     prof_end(K_KL, st, 4.0 * npts * M + 8.0 * S * M + (z_fp32 ? 4.0 : 8.0) * S * npts, 6.0 * npts * M * S);
     MSG_CHECK_LAUNCH();
-    int err = 0;
-    MSG_CUDA_TRY(cudaMemcpyFromSymbolAsync(&err, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
-    MSG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (err) {
-        set_error("sample_field: tensor-core pipeline wait timed out");
-        return MSG_ERR_CUDA;
-    }
+    // a bounded wait that runs out sets g_tc_error (reported by msg_device_status)
     return MSG_OK;
 }
 
 }  // namespace msg
+
+extern "C" int32_t msg_device_status(void)
+{
+    msg::clear_error();
+    MSG_CUDA_TRY(cudaDeviceSynchronize());
+    int err = 0, zero = 0;
+    MSG_CUDA_TRY(cudaMemcpyFromSymbol(&err, msg::g_tc_error, sizeof(int)));
+    MSG_CUDA_TRY(cudaMemcpyToSymbol(msg::g_tc_error, &zero, sizeof(int)));
+    if (err) {
+        msg::set_error("a bounded wait in a tensor-core kernel ran out; its output was not written");
+        return MSG_ERR_TIMEOUT;
+    }
+    return MSG_OK;
+}

@@ -53,8 +53,6 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
     if (S < 0 || p0 < 1 || q0 < 1) { set_error("mimc_differences: need S >= 0, p0 >= 1, q0 >= 1"); return MSG_ERR_INVALID; }
     if (S == 0) return MSG_OK;
     if (!L || !Q || !dQ) { set_error("mimc_differences: NULL pointer"); return MSG_ERR_INVALID; }
-    std::vector<MimcSample> h(S);
-    int64_t qo = 0, dof = 0;
     int maxL1 = 0, maxL2 = 0;
     for (int64_t i = 0; i < S; ++i) {
         int l1 = L[2 * i], l2 = L[2 * i + 1];
@@ -62,9 +60,6 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
             set_error("mimc_differences: multi-index out of range");
             return MSG_ERR_INVALID;
         }
-        h[i] = MimcSample{l1, l2, qo, dof};
-        qo += (int64_t)(p0 + l1) * (q0 + l2);
-        dof += (int64_t)(l1 + 1) * (l2 + 1);
         maxL1 = l1 > maxL1 ? l1 : maxL1;
         maxL2 = l2 > maxL2 ? l2 : maxL2;
     }
@@ -73,23 +68,39 @@ extern "C" int32_t mimc_differences(const int32_t* L, int64_t S, int32_t p0, int
         return MSG_ERR_INVALID;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // tables go through one temporary device block released after the stream drains
-    size_t tb = sizeof(MimcSample) * S, pb = ptau ? sizeof(double) * ld1 * ld2 : 0;
-    char* dbuf = nullptr;
-    MSG_CUDA_TRY(cudaMallocAsync((void**)&dbuf, tb + pb + 256, st));
-    MSG_CUDA_TRY(cudaMemcpyAsync(dbuf, h.data(), tb, cudaMemcpyHostToDevice, st));
-    double* dp = nullptr;
-    if (ptau) {
-        dp = (double*)(dbuf + (tb + 255) / 256 * 256);
-        MSG_CUDA_TRY(cudaMemcpyAsync(dp, ptau, pb, cudaMemcpyHostToDevice, st));
+    // the tables are built in pinned staging (released by an event once copied) and
+    // uploaded into a stream-ordered temporary: the call does not wait for the stream
+    const size_t tb = sizeof(MimcSample) * S, tb_al = (tb + 255) / 256 * 256;
+    const size_t pb = ptau ? sizeof(double) * ld1 * ld2 : 0;
+    void* hp = nullptr;
+    int token = -1;
+    int rc = staging_acquire(tb_al + pb, &hp, &token);
+    if (rc != MSG_OK) return rc;
+    MimcSample* h = (MimcSample*)hp;
+    int64_t qo = 0, dof = 0;
+    for (int64_t i = 0; i < S; ++i) {
+        const int l1 = L[2 * i], l2 = L[2 * i + 1];
+        h[i] = MimcSample{l1, l2, qo, dof};
+        qo += (int64_t)(p0 + l1) * (q0 + l2);
+        dof += (int64_t)(l1 + 1) * (l2 + 1);
     }
+    if (ptau) memcpy((char*)hp + tb_al, ptau, pb);
+    char* dbuf = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dbuf, tb_al + pb + 256, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf, hp, tb_al + pb, cudaMemcpyHostToDevice, st);
+    const int rel = staging_release(token, st);
+    if (e != cudaSuccess) {
+        set_error(std::string("mimc_differences: ") + cudaGetErrorString(e));
+        return MSG_ERR_CUDA;
+    }
+    if (rel != MSG_OK) return rel;
+    const double* dp = ptau ? (const double*)(dbuf + tb_al) : nullptr;
     int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
     prof_begin(K_MIMC, st);
     k_mimc<<<blocks, 256, 0, st>>>((const MimcSample*)dbuf, S, p0, q0, Q, dp, ld2, dQ, Y);
     prof_end(K_MIMC, st, 8.0 * (qo + 2.0 * dof) + tb, 0.0);
     MSG_CHECK_LAUNCH();
     MSG_CUDA_TRY(cudaFreeAsync(dbuf, st));
-    MSG_CUDA_TRY(cudaStreamSynchronize(st));  // the host tables above must outlive the copies
     return MSG_OK;
 }
 

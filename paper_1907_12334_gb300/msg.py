@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-MSG_OK, MSG_ERR_INVALID, MSG_ERR_WORKSPACE, MSG_ERR_CUDA, MSG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+MSG_OK, MSG_ERR_INVALID, MSG_ERR_WORKSPACE, MSG_ERR_CUDA, MSG_ERR_UNSUPPORTED, MSG_ERR_TIMEOUT = 0, 1, 2, 3, 4, 5
 MSG_SAMPLE_NOT_CONVERGED, MSG_SAMPLE_NONFINITE = 1, 2
 MSG_PREC_FP64, MSG_PREC_MIXED = 0, 1
 MSG_QOI_INTEGRAL, MSG_QOI_POINT, MSG_QOI_SUBDOMAIN, MSG_QOI_FLUX = 0, 1, 2, 3
@@ -26,7 +26,7 @@ MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",
             "msg_solve_batch", "msg_solution_values", "msg_solution", "mimc_differences",
-            "mimc_differences_noalloc", "msg_last_error", "msg_version",
+            "mimc_differences_noalloc", "msg_device_status", "msg_last_error", "msg_version",
             "msg_launch_count",
             "msg_profile_enable", "msg_profile_read", "msg_profile_read_level")
 KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
@@ -103,6 +103,8 @@ def load(path: str | None = None):
     L.msg_solution.restype = i32
     L.mimc_differences.argtypes = [vp, i64, i32, i32, vp, vp, i32, i32, vp, vp, vp]
     L.mimc_differences.restype = i32
+    L.msg_device_status.argtypes = []
+    L.msg_device_status.restype = i32
     L.msg_last_error.argtypes = []
     L.msg_last_error.restype = ctypes.c_char_p
     L.msg_version.argtypes = []
@@ -220,6 +222,11 @@ def mimc_differences(L, p0: int, q0: int, Q, dQ, ptau=None, Y=None, stream=None)
         pp = None
     _check(load().mimc_differences(Lh.ctypes.data_as(ctypes.c_void_p), Lh.shape[0], p0, q0, _ptr(Q), pp, ld1, ld2,
                                    _ptr(dQ), _ptr(Y), _stream(stream)))
+
+
+def msg_device_status():
+    """Raise if a bounded wait inside a library kernel ran out since the last call."""
+    _check(load().msg_device_status())
 
 
 def msg_version() -> str:

@@ -273,3 +273,56 @@ def test_uneven_index_set_sampled_against_oracle(msg):
     Qo, _, _ = run_oracle([shapes[i] for i in pick], [Zs[i] for i in pick], 1e-12, 600)
     Qsel = np.concatenate([Qg[offs[i]:offs[i + 1]] for i in pick])
     np.testing.assert_allclose(Qsel, Qo, rtol=1e-8)
+
+
+def test_mimc_differences_is_asynchronous_and_reads_host_tables_before_returning(msg):
+    """The call enqueues its work without waiting for the stream: the host index and
+    p_tau arrays are staged before it returns (overwriting them right after the call
+    changes nothing), and many calls in flight on one stream, each with its own
+    tables, all give the oracle's differences bit for bit."""
+    rng = np.random.default_rng(12)
+    p0, q0 = 1, 2
+    stream = torch.cuda.Stream()
+    calls = []
+    with torch.cuda.stream(stream):
+        for c in range(24):
+            Ls = [(int(a), int(b)) for a, b in rng.integers(0, 4, size=(5 + c, 2))]
+            Qs = [rng.standard_normal((p0 + a, q0 + b)) for a, b in Ls]
+            Qd = torch.from_numpy(np.concatenate([q.ravel() for q in Qs])).to(DEV)
+            nd = sum((a + 1) * (b + 1) for a, b in Ls)
+            dQ = torch.empty(nd, dtype=torch.float64, device=DEV)
+            Y = torch.empty(len(Ls), dtype=torch.float64, device=DEV)
+            Lh = np.array(Ls, dtype=np.int32)
+            ptau = np.exp(-0.9 * (np.arange(4)[:, None] + np.arange(4)[None, :]))
+            msg.mimc_differences(Lh, p0, q0, Qd, dQ, ptau=ptau, Y=Y, stream=stream)
+            Lh[:] = 7  # the library must not read these after returning
+            ptau[:] = np.nan
+            calls.append((Ls, Qs, Qd, dQ, Y))
+    stream.synchronize()
+    ptau = np.exp(-0.9 * (np.arange(4)[:, None] + np.arange(4)[None, :]))
+    for Ls, Qs, _, dQ, Y in calls:
+        off = 0
+        for k, (L, Qg) in enumerate(zip(Ls, Qs)):
+            d_o, y_o = oracle.mimc_differences(L, p0, q0, Qg, ptau=ptau)
+            assert np.array_equal(dQ[off:off + d_o.size].cpu().numpy(), d_o.ravel())
+            assert Y[k].item() == y_o
+            off += d_o.size
+
+
+def test_bf16x3_sampler_reports_through_the_status_query(msg):
+    """The tensor-core sampler no longer stops the stream to read its pipeline flag;
+    msg_device_status reports a bounded wait that ran out (none here)."""
+    P, Q, M, S = 3, 3, 40, 130
+    Phi, sl = inputs.kl_basis(P, Q, inputs.small_law(M))
+    npts = Phi.shape[0]
+    m = msg.MSG_GEMM_BF16X3
+    prep = torch.empty(msg.kl_prepared_bytes(npts, M, m), dtype=torch.uint8, device=DEV)
+    msg.kl_prepare(torch.from_numpy(np.ascontiguousarray(Phi)).to(DEV), torch.from_numpy(sl.copy()).to(DEV), m, prep)
+    xi = torch.empty((S, M), dtype=torch.float64, device=DEV)
+    msg.msg_normals(3, 0, S, M, xi)
+    Z = torch.empty((S, npts), dtype=torch.float64, device=DEV)
+    msg.sample_field(prep, npts, M, m, xi, Z)
+    msg.msg_device_status()  # raises on MSG_ERR_TIMEOUT
+    Zo = np.stack([oracle.kl_field(Phi, sl, oracle.normals(3, i, M)) for i in range(S)])
+    scale = np.abs(Phi * sl).sum(axis=1)[None, :] * np.abs(Zo).max()
+    assert np.all(np.abs(Z.cpu().numpy() - Zo) <= 5e-5 * np.maximum(scale, 1.0))
