@@ -67,6 +67,7 @@ extern "C" {
 #define MSG_GEMM_FP64 0  /* FP64 products and sums */
 #define MSG_GEMM_BF16X3 1 /* tensor cores: bf16 hi/lo splits, hi*hi + hi*lo + lo*hi, FP32 accumulate */
 #define MSG_GEMM_FP32 2  /* FP32 products and sums (SIMT) */
+#define MSG_GEMM_TF32 3  /* tensor cores: both operands rounded to TF32, one product per term, FP32 accumulate */
 
 /* Solver parameters (Sec. 2 and its numerical setup: W(2,2) cycles, mu = 2,
  * red-black Gauss-Seidel, damping omega of the coarse-grid correction,
@@ -105,7 +106,8 @@ int32_t msg_normals(uint64_t seed, uint64_t s0, int64_t S, int32_t M, double* xi
 /*                                                                          */
 /* kl_prepare converts the FP64 basis once into the layout `mode` uses:      */
 /*   Phi, sqrt_lambda [device] double, read.                                 */
-/*   prepared [device] bytes >= kl_prepared_bytes(npts, M, mode), written.   */
+/*   prepared [device] bytes >= kl_prepared_bytes(npts, M, mode), written;   */
+/*            256-byte aligned for the tensor-core modes.                     */
 /* sample_field contracts it with xi:                                       */
 /*   xi [device] double [S][M], read.                                        */
 /*   Z  [device] double [S][npts] (or float if z_fp32 != 0), written.         */

@@ -147,7 +147,8 @@ extern "C" size_t kl_prepared_bytes(int64_t npts, int32_t M, int32_t mode)
     switch (mode) {
     case MSG_GEMM_FP64: return align256(sizeof(double) * npts * M) + align256(sizeof(double) * M);
     case MSG_GEMM_FP32: return align256(sizeof(float) * npts * M) + align256(sizeof(double) * M);
-    case MSG_GEMM_BF16X3: return kl_tc_prepared_bytes(npts, M);
+    case MSG_GEMM_BF16X3:
+    case MSG_GEMM_TF32: return kl_tc_prepared_bytes(npts, M, mode);
     default: return 0;
     }
 }
@@ -165,7 +166,10 @@ extern "C" int32_t kl_prepare(const double* Phi, const double* sqrt_lambda, int6
     if (prepared_bytes < need) { set_error("kl_prepare: buffer too small"); return MSG_ERR_WORKSPACE; }
     cudaStream_t st = (cudaStream_t)stream;
     char* base = (char*)prepared;
-    if (mode == MSG_GEMM_BF16X3) return kl_tc_prepare(Phi, sqrt_lambda, npts, M, prepared, st);
+    if (mode == MSG_GEMM_BF16X3 || mode == MSG_GEMM_TF32) {
+        if ((uintptr_t)prepared % 256) { set_error("kl_prepare: prepared buffer must be 256-byte aligned"); return MSG_ERR_INVALID; }
+        return kl_tc_prepare(Phi, sqrt_lambda, npts, M, mode, prepared, st);
+    }
     if (mode == MSG_GEMM_FP64) {
         MSG_CUDA_TRY(cudaMemcpyAsync(base, Phi, sizeof(double) * npts * M, cudaMemcpyDeviceToDevice, st));
         MSG_CUDA_TRY(cudaMemcpyAsync(base + align256(sizeof(double) * npts * M), sqrt_lambda, sizeof(double) * M,
@@ -189,7 +193,10 @@ extern "C" int32_t sample_field(const void* prepared, int64_t npts, int32_t M, i
     if (S == 0) return MSG_OK;
     if (!prepared || !xi || !Z) { set_error("sample_field: NULL pointer"); return MSG_ERR_INVALID; }
     cudaStream_t st = (cudaStream_t)stream;
-    if (mode == MSG_GEMM_BF16X3) return kl_tc_sample(prepared, npts, M, xi, S, Z, z_fp32, st);
+    if (mode == MSG_GEMM_BF16X3 || mode == MSG_GEMM_TF32) {
+        if ((uintptr_t)prepared % 256) { set_error("sample_field: prepared buffer must be 256-byte aligned"); return MSG_ERR_INVALID; }
+        return kl_tc_sample(prepared, npts, M, mode, xi, S, Z, z_fp32, st);
+    }
     if (S > 65535LL * 64) { set_error("sample_field: too many samples for one call"); return MSG_ERR_INVALID; }
     dim3 grid((unsigned)((npts + 63) / 64), (unsigned)((S + 63) / 64));
     const char* base = (const char*)prepared;

@@ -1,21 +1,26 @@
 // kl_tc.cu -- KL contraction Z = Phi diag(sqrt(lambda)) xi on the 5th-generation
-// tensor cores (tcgen05), BF16x3 split products with FP32 accumulation.
+// tensor cores (tcgen05) with FP32 accumulation, in two operand modes:
+//   BF16X3  each operand v is split into bf16 parts v = hi + lo + O(2^-16 |v|) and
+//           the product uses hi*hi + hi*lo + lo*hi (kind::f16), about 1e-5 of
+//           sum_m |A B| -- the lo*lo term and the remainders are below the FP32
+//           accumulation of a 400-term sum of unit-scale products;
+//   TF32    both operands rounded to TF32 (10-bit mantissa, round to nearest) and
+//           one product per term (kind::tf32), about 1e-3 of sum_m |A B|.
+// Neither is the FP64 path; the sampler's error is stated per result in the tests
+// and the bench.
 //
 // Z[s][x] = sum_m A[s][m] B[x][m] with A = sqrt(lambda) * xi (samples x terms)
-// and B = Phi (points x terms).  Each operand v is split into bf16 parts
-// v = hi + lo + O(2^-16 |v|); the product uses hi*hi + hi*lo + lo*hi (the
-// lo*lo term and the remainders are below the FP32 accumulation of a 400-term
-// sum of unit-scale products), so Z carries a relative error of about 1e-5 of
-// sum_m |A B| -- the sampler is not the FP64 path; its error is stated per
-// result in the tests.
-//
-// One CTA computes a 128 (samples) x 256 (points) tile of Z: accumulators in
-// 256 TMEM columns, K in chunks of 64 bf16 staged through two shared-memory
-// stages in the 128-byte-swizzled K-major layout the UMMA descriptors expect.
-// A is split on the fly from FP64 xi and sqrt(lambda); B (Phi) is split once
-// by kl_tc_prepare into zero-padded [Np][Kp] bf16 arrays.  One elected thread
-// issues the MMAs and commits them to an mbarrier per stage; every wait is
-// bounded and a timeout sets an error flag instead of hanging.
+// and B = Phi (points x terms).  One CTA computes a 128 (samples) x 256 (points)
+// tile of Z: accumulators in 256 TMEM columns, K in 128-byte chunks (64 bf16 or
+// 32 TF32 terms) staged through two shared-memory stages in the 128-byte-swizzled
+// K-major layout the UMMA descriptors expect.  A is converted on the fly from FP64
+// xi and sqrt(lambda); B is converted once by kl_tc_prepare into zero-padded
+// [Np][Kp] part arrays and its tiles arrive by 16-byte asynchronous copies
+// (cp.async) while the A chunk is being converted.  One elected thread issues the
+// MMAs and commits them to an mbarrier per stage; every wait is bounded and a
+// timeout sets a device flag (read by msg_device_status) instead of hanging.  The
+// epilogue moves each warp's 32 x 32 accumulator blocks through shared memory so
+// that every global store of a warp writes 32 consecutive points of one sample.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -28,21 +33,35 @@ namespace {
 
 constexpr int kTM = 128;  // samples per tile (UMMA M)
 constexpr int kTN = 256;  // points per tile (UMMA N)
-constexpr int kTK = 64;   // K chunk: 64 bf16 = one 128-byte swizzle row
 constexpr int kThreadsTC = 256;
-constexpr int kAbytes = kTM * kTK * 2;       // 16 KB per A part
-constexpr int kBbytes = kTN * kTK * 2;       // 32 KB per B part
-constexpr int kStageBytes = 2 * kAbytes + 2 * kBbytes;  // hi+lo of A and B: 96 KB
-constexpr int kSmemBytes = 2 * kStageBytes + 1024;      // two stages + alignment slack
-constexpr long long kSpinLimit = 1ll << 22;             // bounded mbarrier waits (seconds)
+constexpr int kRowBytes = 128;                        // one swizzled K row
+constexpr int kAbytes = kTM * kRowBytes;              // 16 KB per A part and stage
+constexpr int kBbytes = kTN * kRowBytes;              // 32 KB per B part and stage
+constexpr long long kSpinLimit = 1ll << 22;           // bounded mbarrier waits (seconds)
+
+// Operand modes of the tensor-core kernel.
+enum { TC_BF16X3 = 0, TC_TF32 = 1 };
+template <int MODE> struct TcCfg;
+template <> struct TcCfg<TC_BF16X3> {
+    typedef __nv_bfloat16 E;
+    static constexpr int parts = 2;  // hi, lo
+    static constexpr int TK = 64;    // terms per 128-byte row
+};
+template <> struct TcCfg<TC_TF32> {
+    typedef float E;
+    static constexpr int parts = 1;
+    static constexpr int TK = 32;
+};
+template <int MODE> constexpr int stage_bytes() { return TcCfg<MODE>::parts * (kAbytes + kBbytes); }
+template <int MODE> constexpr int smem_bytes() { return 2 * stage_bytes<MODE>() + 1024; }  // + alignment slack
 
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 __device__ int g_tc_error;  // set by a kernel whose mbarrier wait ran out (sticky until msg_device_status)
 
-// Byte offset of element (r, k), 0 <= k < 64, in a K-major tile with the
-// 128-byte swizzle: 8-row atoms of 1024 bytes, 16-byte chunk c of row rr
-// stored at chunk position c ^ rr.
+// Byte offset of 16-byte chunk `chunk` (0..7) of row r in a K-major tile with the
+// 128-byte swizzle: 8-row atoms of 1024 bytes, chunk c of row rr stored at
+// chunk position c ^ rr.
 __device__ __forceinline__ uint32_t sw128(int r, int chunk) { return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4); }
 
 // tcgen05 shared-memory matrix descriptor: start address >> 4 in bits 0-13,
@@ -55,11 +74,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
            (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+// Instruction descriptor: D = F32 (bits 4-5 = 1); A and B formats in bits 7-9
+// and 10-12 (kind::f16: 1 = BF16; kind::tf32: 2 = TF32), both K-major;
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <int MODE>
 __host__ __device__ constexpr uint32_t instr_desc()
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+    return (1u << 4) | ((MODE == TC_TF32 ? 2u : 1u) << 7) | ((MODE == TC_TF32 ? 2u : 1u) << 10) |
+           ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,14 +109,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
+    if constexpr (MODE == TC_TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(instr_desc<MODE>()), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(instr_desc<MODE>()), "r"(acc)
+            : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
@@ -127,6 +158,16 @@ __device__ __forceinline__ void split2(double v, __nv_bfloat16& hi, __nv_bfloat1
     lo = __double2bfloat16(v - (double)__bfloat162float(hi));
 }
 
+// FP64 -> TF32 (round to nearest, ties away), kept in an FP32 container.
+__device__ __forceinline__ float to_tf32(double v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+    return __uint_as_float(r);
+}
+
+// Operand conversion of 8 consecutive terms into the parts of one 16-byte chunk
+// (BF16X3: 8 terms -> 16 bytes per part; TF32: 4 terms -> 16 bytes).
 __global__ void k_split_phi(const double* Phi, int64_t npts, int M, int64_t Kp, int64_t Np, __nv_bfloat16* Bhi,
                             __nv_bfloat16* Blo)
 {
@@ -141,12 +182,28 @@ __global__ void k_split_phi(const double* Phi, int64_t npts, int M, int64_t Kp, 
     }
 }
 
-template <class TZ>
+__global__ void k_tf32_phi(const double* Phi, int64_t npts, int M, int64_t Kp, int64_t Np, float* B)
+{
+    const int64_t n = Np * Kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = e / Kp, m = e % Kp;
+        B[e] = (x < npts && m < M) ? to_tf32(Phi[x * M + m]) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <int MODE, class TZ>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_kl_tc(const __nv_bfloat16* __restrict__ Bhi, const __nv_bfloat16* __restrict__ Blo,
+    k_kl_tc(const typename TcCfg<MODE>::E* __restrict__ B0, const typename TcCfg<MODE>::E* __restrict__ B1,
             const double* __restrict__ sl, const double* __restrict__ xi, int64_t npts, int M, int64_t Kp, int64_t S,
             TZ* __restrict__ Z)
 {
+    typedef typename TcCfg<MODE>::E E;
+    constexpr int parts = TcCfg<MODE>::parts, TK = TcCfg<MODE>::TK, EPC = 16 / (int)sizeof(E);  // terms per chunk
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_base_slot;
@@ -172,52 +229,62 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_slot;
 
-    const int nchunks = (int)(Kp / kTK);
-    const uint32_t idesc = instr_desc();
+    const int nchunks = (int)(Kp / TK);
     bool ok = true;
     for (int kc = 0; kc < nchunks; ++kc) {
         const int st = kc & 1;
-        unsigned char* sA_hi = base + st * kStageBytes;
-        unsigned char* sA_lo = sA_hi + kAbytes;
-        unsigned char* sB_hi = sA_lo + kAbytes;
-        unsigned char* sB_lo = sB_hi + kBbytes;
+        unsigned char* sA = base + st * stage_bytes<MODE>();  // A parts, then B parts
+        unsigned char* sB = sA + parts * kAbytes;
         if (kc >= 2) ok &= mbar_wait(&bars[st], ((kc >> 1) - 1) & 1);  // the MMAs that read this stage are done
-        // A chunk: 128 rows x 8 chunks of 8 terms, split on the fly
+        // B chunk: 256 rows x 8 chunks per part, already converted and zero padded
+        for (int t = tid; t < kTN * 8; t += kThreadsTC) {
+            const int r = t >> 3, c = t & 7;
+            const int64_t g = (x0 + r) * Kp + (int64_t)kc * TK + c * EPC;
+            const uint32_t off = sw128(r, c);
+            cp_async16(smem_u32(sB + off), B0 + g);
+            if constexpr (parts == 2) cp_async16(smem_u32(sB + kBbytes + off), B1 + g);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // A chunk: 128 rows x 8 chunks, converted on the fly while B is in flight
         for (int t = tid; t < kTM * 8; t += kThreadsTC) {
             const int r = t >> 3, c = t & 7;
             const int64_t s = s0 + r;
-            __align__(16) __nv_bfloat16 h[8], l[8];
+            const uint32_t off = sw128(r, c);
+            if constexpr (MODE == TC_BF16X3) {
+                __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int m = kc * kTK + c * 8 + j;
-                double v = (s < S && m < M) ? sl[m] * xi[s * M + m] : 0.0;
-                split2(v, h[j], l[j]);
+                for (int j = 0; j < 8; ++j) {
+                    const int m = kc * TK + c * 8 + j;
+                    double v = (s < S && m < M) ? sl[m] * xi[s * M + m] : 0.0;
+                    split2(v, h[j], l[j]);
+                }
+                *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(h);
+                *reinterpret_cast<uint4*>(sA + kAbytes + off) = *reinterpret_cast<const uint4*>(l);
+            } else {
+                __align__(16) float f[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = kc * TK + c * 4 + j;
+                    f[j] = (s < S && m < M) ? to_tf32(sl[m] * xi[s * M + m]) : 0.f;
+                }
+                *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(f);
             }
-            const uint32_t off = sw128(r, c);
-            *reinterpret_cast<uint4*>(sA_hi + off) = *reinterpret_cast<const uint4*>(h);
-            *reinterpret_cast<uint4*>(sA_lo + off) = *reinterpret_cast<const uint4*>(l);
         }
-        // B chunk: 256 rows x 8 chunks, already split and zero padded
-        for (int t = tid; t < kTN * 8; t += kThreadsTC) {
-            const int r = t >> 3, c = t & 7;
-            const int64_t g = (x0 + r) * Kp + (int64_t)kc * kTK + c * 8;
-            const uint32_t off = sw128(r, c);
-            *reinterpret_cast<uint4*>(sB_hi + off) = *reinterpret_cast<const uint4*>(Bhi + g);
-            *reinterpret_cast<uint4*>(sB_lo + off) = *reinterpret_cast<const uint4*>(Blo + g);
-        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make the stores visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(sA_hi), a_lo = smem_u32(sA_lo);
-            const uint32_t b_hi = smem_u32(sB_hi), b_lo = smem_u32(sB_lo);
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
-            for (int k16 = 0; k16 < kTK / 16; ++k16) {
-                const uint32_t ko = k16 * 32;  // 16 bf16 = 32 bytes along the swizzled row
-                const uint32_t first = (kc == 0 && k16 == 0) ? 0u : 1u;
-                mma_bf16(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), idesc, first);
-                mma_bf16(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1u);
-                mma_bf16(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
+            for (int ks = 0; ks < 4; ++ks) {  // 4 MMA K steps of 32 bytes per 128-byte row
+                const uint32_t ko = ks * 32;
+                const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+                mma<MODE>(tmem, smem_desc(a0 + ko), smem_desc(b0 + ko), first);
+                if constexpr (MODE == TC_BF16X3) {
+                    mma<MODE>(tmem, smem_desc(a0 + ko), smem_desc(b0 + kBbytes + ko), 1u);            // hi * lo
+                    mma<MODE>(tmem, smem_desc(a0 + kAbytes + ko), smem_desc(b0 + ko), 1u);            // lo * hi
+                }
             }
             mma_commit(&bars[st]);
         }
@@ -226,22 +293,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (nchunks >= 2) ok &= mbar_wait(&bars[(nchunks - 2) & 1], ((nchunks - 2) >> 1) & 1);
     if (nchunks >= 1) ok &= mbar_wait(&bars[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-        if (lane == 0) atomicExch(&g_tc_error, 1);
+    // every thread took part in the same waits; make the decision CTA-wide
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
+    if (!all_ok) {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 128 (w / 4) .. +127
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (samples), columns 128 (w / 4) .. +127
+        // (points); each 32 x 32 block goes through a padded shared tile so that the stores of a
+        // warp cover 32 consecutive points of one sample
         const int lane_base = 32 * (warp & 3), col_base = 128 * (warp >> 2);
-        const int64_t s = s0 + lane_base + lane;
+        float* tile = reinterpret_cast<float*>(base) + warp * 32 * 33;  // the stages are free now
         for (int cb = 0; cb < 128; cb += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(col_base + cb), v);
-            if (s < S) {
-                const int64_t xb = x0 + col_base + cb;
-                TZ* out = Z + s * npts + xb;
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (xb + k < npts) out[k] = (TZ)v[k];
+            for (int k = 0; k < 32; ++k) tile[lane * 33 + k] = v[k];
+            __syncwarp();
+            const int64_t x = x0 + col_base + cb + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int64_t s = s0 + lane_base + rr;
+                if (s < S && x < npts) Z[s * npts + x] = (TZ)tile[rr * 33 + lane];
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -252,60 +325,78 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
 struct TcLayout {
     int64_t Kp, Np;
-    size_t hi, lo, sl, total;
+    size_t p0, p1, sl, total;
 };
 
-TcLayout tc_layout(int64_t npts, int32_t M)
+TcLayout tc_layout(int64_t npts, int32_t M, int mode)
 {
     TcLayout L{};
-    L.Kp = round_up(M, kTK);
+    const bool tf = mode == TC_TF32;
+    L.Kp = round_up(M, tf ? TcCfg<TC_TF32>::TK : TcCfg<TC_BF16X3>::TK);
     L.Np = round_up(npts, kTN);
-    const size_t part = (size_t)L.Np * L.Kp * sizeof(__nv_bfloat16);
-    L.hi = 0;
-    L.lo = (part + 255) / 256 * 256;
-    L.sl = L.lo + L.lo;
+    const size_t part = (size_t)L.Np * L.Kp * (tf ? sizeof(float) : sizeof(__nv_bfloat16));
+    L.p0 = 0;
+    L.p1 = (part + 255) / 256 * 256;
+    L.sl = tf ? L.p1 : 2 * L.p1;
     L.total = L.sl + ((sizeof(double) * M + 255) / 256 * 256);
     return L;
 }
 
+int tc_mode(int32_t gemm_mode) { return gemm_mode == MSG_GEMM_TF32 ? TC_TF32 : TC_BF16X3; }
+
+template <int MODE, class TZ>
+int tc_launch(const TcLayout& L, const char* b, int64_t npts, int32_t M, const double* xi, int64_t S, void* Z,
+              cudaStream_t st)
+{
+    typedef typename TcCfg<MODE>::E E;
+    dim3 grid((unsigned)(L.Np / kTN), (unsigned)((S + kTM - 1) / kTM));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<MODE>()));
+    k_kl_tc<MODE, TZ><<<grid, kThreadsTC, smem_bytes<MODE>(), st>>>((const E*)(b + L.p0), (const E*)(b + L.p1),
+                                                                     (const double*)(b + L.sl), xi, npts, M, L.Kp, S,
+                                                                     (TZ*)Z);
+    return MSG_OK;
+}
+
 }  // namespace
 
-size_t kl_tc_prepared_bytes(int64_t npts, int32_t M) { return tc_layout(npts, M).total; }
+size_t kl_tc_prepared_bytes(int64_t npts, int32_t M, int32_t mode) { return tc_layout(npts, M, tc_mode(mode)).total; }
 
-int32_t kl_tc_prepare(const double* Phi, const double* sqrt_lambda, int64_t npts, int32_t M, void* prepared,
-                      cudaStream_t st)
+int32_t kl_tc_prepare(const double* Phi, const double* sqrt_lambda, int64_t npts, int32_t M, int32_t mode,
+                      void* prepared, cudaStream_t st)
 {
-    const TcLayout L = tc_layout(npts, M);
+    const int tm = tc_mode(mode);
+    const TcLayout L = tc_layout(npts, M, tm);
     char* b = (char*)prepared;
     prof_begin(K_KL, st);
-    k_split_phi<<<152 * 8, 256, 0, st>>>(Phi, npts, M, L.Kp, L.Np, (__nv_bfloat16*)(b + L.hi),
-                                          (__nv_bfloat16*)(b + L.lo));
+    if (tm == TC_TF32)
+        k_tf32_phi<<<152 * 8, 256, 0, st>>>(Phi, npts, M, L.Kp, L.Np, (float*)(b + L.p0));
+    else
+        k_split_phi<<<152 * 8, 256, 0, st>>>(Phi, npts, M, L.Kp, L.Np, (__nv_bfloat16*)(b + L.p0),
+                                              (__nv_bfloat16*)(b + L.p1));
     prof_end(K_KL, st, 8.0 * npts * M + 4.0 * L.Np * L.Kp, 0.0);
     MSG_CHECK_LAUNCH();
     MSG_CUDA_TRY(cudaMemcpyAsync(b + L.sl, sqrt_lambda, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
     return MSG_OK;
 }
 
-int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, const double* xi, int64_t S, void* Z,
+int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, int32_t mode, const double* xi, int64_t S, void* Z,
                      int32_t z_fp32, cudaStream_t st)
 {
-    const TcLayout L = tc_layout(npts, M);
+    const int tm = tc_mode(mode);
+    const TcLayout L = tc_layout(npts, M, tm);
     if ((S + kTM - 1) / kTM > 65535) { set_error("sample_field: too many samples for one call"); return MSG_ERR_INVALID; }
     const char* b = (const char*)prepared;
-    const __nv_bfloat16* Bhi = (const __nv_bfloat16*)(b + L.hi);
-    const __nv_bfloat16* Blo = (const __nv_bfloat16*)(b + L.lo);
-    const double* sl = (const double*)(b + L.sl);
-    dim3 grid((unsigned)(L.Np / kTN), (unsigned)((S + kTM - 1) / kTM));
     prof_begin(K_KL, st);
-    if (z_fp32) {
-        MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        k_kl_tc<float><<<grid, kThreadsTC, kSmemBytes, st>>>(Bhi, Blo, sl, xi, npts, M, L.Kp, S, (float*)Z);
-    } else {
-        MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        k_kl_tc<double><<<grid, kThreadsTC, kSmemBytes, st>>>(Bhi, Blo, sl, xi, npts, M, L.Kp, S, (double*)Z);
-    }
-    // algorithmic work: 3 split products of 2 npts M S flops; bytes: Phi parts, xi, Z
-    prof_end(K_KL, st, 4.0 * npts * M + 8.0 * S * M + (z_fp32 ? 4.0 : 8.0) * S * npts, 6.0 * npts * M * S);
+    int rc;
+    if (tm == TC_TF32)
+        rc = z_fp32 ? tc_launch<TC_TF32, float>(L, b, npts, M, xi, S, Z, st) : tc_launch<TC_TF32, double>(L, b, npts, M, xi, S, Z, st);
+    else
+        rc = z_fp32 ? tc_launch<TC_BF16X3, float>(L, b, npts, M, xi, S, Z, st)
+                    : tc_launch<TC_BF16X3, double>(L, b, npts, M, xi, S, Z, st);
+    if (rc != MSG_OK) return rc;
+    // algorithmic work: (3 split products or 1) of 2 npts M S flops; bytes: Phi parts, xi, Z
+    const double parts = tm == TC_TF32 ? 1.0 : 3.0, pbytes = tm == TC_TF32 ? 4.0 : 4.0;
+    prof_end(K_KL, st, pbytes * npts * M + 8.0 * S * M + (z_fp32 ? 4.0 : 8.0) * S * npts, 2.0 * parts * npts * M * S);
     MSG_CHECK_LAUNCH();
     // a bounded wait that runs out sets g_tc_error (reported by msg_device_status)
     return MSG_OK;

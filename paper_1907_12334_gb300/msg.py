@@ -21,7 +21,7 @@ MSG_OK, MSG_ERR_INVALID, MSG_ERR_WORKSPACE, MSG_ERR_CUDA, MSG_ERR_UNSUPPORTED, M
 MSG_SAMPLE_NOT_CONVERGED, MSG_SAMPLE_NONFINITE = 1, 2
 MSG_PREC_FP64, MSG_PREC_MIXED = 0, 1
 MSG_QOI_INTEGRAL, MSG_QOI_POINT, MSG_QOI_SUBDOMAIN, MSG_QOI_FLUX = 0, 1, 2, 3
-MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32 = 0, 1, 2
+MSG_GEMM_FP64, MSG_GEMM_BF16X3, MSG_GEMM_FP32, MSG_GEMM_TF32 = 0, 1, 2, 3
 MSG_COEF_SERIES, MSG_COEF_INJECT = 0, 1
 
 EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "msg_workspace_bytes",

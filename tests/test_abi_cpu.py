@@ -97,6 +97,10 @@ def test_kl_prepared_bytes(lib):
     assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_FP64) >= 100 * 16 * 8
     assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_FP32) >= 100 * 16 * 4
     assert msg.kl_prepared_bytes(100, 16, 99) == 0
+    # tensor-core modes: Phi padded to whole 256-point tiles and 128-byte K rows
+    assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_BF16X3) >= 2 * 256 * 64 * 2
+    assert msg.kl_prepared_bytes(100, 16, msg.MSG_GEMM_TF32) >= 256 * 32 * 4
+    assert msg.kl_prepared_bytes(300, 400, msg.MSG_GEMM_TF32) >= 512 * 416 * 4
 
 
 def test_mimc_rejects_bad_indices(lib):
