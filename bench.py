@@ -64,6 +64,13 @@ def parse():
                     help="also time one step of S samples through the batched path with FP64 cycles "
                          "(separates the batching gain from the precision gain; 0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass (at most --steps)")
+    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving"],
+                    help="solve: the batched FMSG solve (default line); kl: KL field sampling at 1024^2 points, "
+                         "M = 400, 8192 samples, every GEMM mode; uneven: 16 384 samples over grids 4..512 per "
+                         "side in one call; serving: adaptive MIMC driver requests through continuous batching")
+    ap.add_argument("--kl-n", type=int, default=1024, help="kl workload: points per side")
+    ap.add_argument("--kl-S", type=int, default=8192, help="kl workload: samples")
+    ap.add_argument("--kl-chunk", type=int, default=1024, help="kl workload: samples per call")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -474,6 +481,233 @@ def unconverged_breakdown(status, cycles, relres, P, Q, eps, max_cycles):
             "counted_in_value": False}
 
 
+# ------------------------------------------------------- KL sampling workload --
+
+def kl_workload(a):
+    """KL field sampling: Z = Phi diag(sqrt(lambda)) xi at n^2 points, M terms, S samples
+    (called in chunks of kl_chunk samples), FP32 output, every GEMM mode of sample_field;
+    time on the device with CUDA events and max abs error of Z against the FP64 mode on
+    the first samples."""
+    import torch
+
+    from paper_1907_12334_gb300 import build, inputs, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n, M, S, chunk = a.kl_n, a.M, a.kl_S, min(a.kl_chunk, a.kl_S)
+    npts = n * n
+    law = inputs.FieldLaw(M=M)
+    Phi_d = torch.empty((npts, M), dtype=torch.float64, device=dev)
+    step = max(1, (1 << 24) // (n * M))
+    for r0 in range(0, n, step):
+        rows = np.arange(r0, min(n, r0 + step))
+        Pb, sl = inputs.kl_basis_nodes(n, n, law, rows=rows)
+        Phi_d[r0 * n:(r0 + rows.size) * n].copy_(torch.from_numpy(Pb))
+    sl_d = torch.from_numpy(np.array(sl)).to(dev)
+    seed = 4
+    xi = torch.empty((S, M), dtype=torch.float64, device=dev)
+    msg.msg_normals(seed, 0, S, M, xi)
+    nref = min(64, S)
+    modes = {"FP64": msg.MSG_GEMM_FP64, "FP32": msg.MSG_GEMM_FP32, "BF16X3": msg.MSG_GEMM_BF16X3,
+             "TF32": msg.MSG_GEMM_TF32}
+    preps = {}
+    for name, m in modes.items():
+        preps[name] = torch.empty(msg.kl_prepared_bytes(npts, M, m), dtype=torch.uint8, device=dev)
+        msg.kl_prepare(Phi_d, sl_d, m, preps[name])
+    del Phi_d
+    Zref = torch.empty((nref, npts), dtype=torch.float64, device=dev)
+    msg.sample_field(preps["FP64"], npts, M, msg.MSG_GEMM_FP64, xi[:nref], Zref)
+    Zc = torch.empty((chunk, npts), dtype=torch.float32, device=dev)
+    Zt = torch.empty((nref, npts), dtype=torch.float64, device=dev)
+    hbm, bf16, _ = measured_peaks()
+    peaks = {"BF16X3": bf16, "TF32": bf16 * 1.1 / 2.25}
+    out = {}
+    for name, m in modes.items():
+        msg.sample_field(preps[name], npts, M, m, xi[:chunk], Zc)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c0 in range(0, S, chunk):
+            msg.sample_field(preps[name], npts, M, m, xi[c0:c0 + chunk], Zc)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        msg.msg_device_status()
+        t = e0.elapsed_time(e1) / 1000.0
+        msg.sample_field(preps[name], npts, M, m, xi[:nref], Zt)
+        err = float((Zt - Zref).abs().max())
+        zmax = float(Zref.abs().max())
+        flops = 2.0 * npts * M * S
+        tensor = 3.0 * flops if name == "BF16X3" else flops
+        r = {"s": t, "samples_per_s": S / t, "tflops_algorithmic": flops / t / 1e12,
+             "max_abs_err_vs_fp64": err, "max_abs_Z": zmax, "output_GBps": 4.0 * npts * S / t / 1e9}
+        if name in peaks:
+            r.update({"tensor_tflops": tensor / t / 1e12, "tensor_peak_tflops": peaks[name],
+                      "frac_of_tensor_peak": tensor / t / 1e12 / peaks[name]})
+        out[name] = r
+    best = out["BF16X3"]
+    line = {
+        "metric": "KL field samples/s", "value": best["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "bf16x3 (fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"KL field sampling, {n}x{n} points, M={M} terms, S={S} samples in calls of {chunk}, "
+                               "xi ~ N(0,1) FP64 (Philox), Z written as FP32", "npts": npts, "M": M, "S": S},
+        "modes": out,
+        "roofline": {"bound": "tensor", "kernel": "k_kl_tc (BF16X3)", "achieved": best["tensor_tflops"],
+                     "peak": best["tensor_peak_tflops"], "unit": "TFLOP/s", "frac": best["frac_of_tensor_peak"],
+                     "peak_source": "measured bf16 (MEASURED_PEAKS.json); TF32 peak = measured bf16 x 1.1/2.25 "
+                                    "(nominal ratio)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ uneven workload --
+
+def uneven_workload(a):
+    """16 384 samples, 256 per multi-index (a1, a2) in 0..7^2, finest grid 2^(a1+2) x 2^(a2+2)
+    (4..512 cells per side), shuffled into one msg_solve_batch call; fields from the same
+    Matern law (KL, M terms, FP32 contraction).  Reports the whole call's samples/s and each
+    shape class solved on its own, and checks a few samples (one 512 cells wide) against the
+    oracle on fields the oracle builds itself."""
+    import torch
+
+    import oracle
+    from paper_1907_12334_gb300 import build, inputs, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    M, per, seed = a.M, 256, 11
+    shapes = inputs.uneven_shapes(per * 64, k=2, amax=7, seed=3)
+    S = len(shapes)
+    PQ = np.array(shapes, dtype=np.int32)
+    npf = np.array([msg.field_points(int(P), int(Q)) for P, Q in shapes], dtype=np.int64)
+    foff = np.concatenate([[0], np.cumsum(npf)])
+    Z = torch.empty(int(foff[-1]), dtype=torch.float64, device=dev)
+    law = inputs.FieldLaw(M=M)
+    by_shape = {}
+    for i, pq in enumerate(shapes):
+        by_shape.setdefault(tuple(pq), []).append(i)
+    for (P, Q), idx in sorted(by_shape.items()):  # untimed input construction, one basis at a time
+        Phi, sl = inputs.kl_basis(P, Q, law)
+        npts = Phi.shape[0]
+        prep = torch.empty(msg.kl_prepared_bytes(npts, M, msg.MSG_GEMM_FP32), dtype=torch.uint8, device=dev)
+        msg.kl_prepare(torch.from_numpy(np.ascontiguousarray(Phi)).to(dev), torch.from_numpy(np.array(sl)).to(dev),
+                       msg.MSG_GEMM_FP32, prep)
+        xi = torch.empty((len(idx), M), dtype=torch.float64, device=dev)
+        Zs = torch.empty((len(idx), npts), dtype=torch.float64, device=dev)
+        for k, i in enumerate(idx):
+            msg.msg_normals(seed, i, 1, M, xi[k:k + 1])
+        msg.sample_field(prep, npts, M, msg.MSG_GEMM_FP32, xi, Zs)
+        for k, i in enumerate(idx):
+            Z[int(foff[i]):int(foff[i + 1])].copy_(Zs[k])
+        inputs.kl_basis.cache_clear()
+    prm = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega)
+    nq = int((PQ[:, 0].astype(np.int64) * PQ[:, 1]).sum())
+    Qout = torch.empty(nq, dtype=torch.float64, device=dev)
+    status = torch.empty(S, dtype=torch.int32, device=dev)
+    cycles = torch.empty(nq, dtype=torch.int32, device=dev)
+    relres = torch.empty(nq, dtype=torch.float64, device=dev)
+    ws = torch.empty(msg.msg_workspace_bytes(PQ, prm), dtype=torch.uint8, device=dev)
+    for _ in range(max(a.warmup, 1)):
+        msg.msg_solve_batch(PQ, prm, Z, Qout, status, cycles, relres, ws)
+    torch.cuda.synchronize(dev)
+    l0 = msg.msg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(a.steps):
+            msg.msg_solve_batch(PQ, prm, Z, Qout, status, cycles, relres, ws)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1000.0
+    launches = msg.msg_launch_count() - l0
+    st = status.cpu().numpy()
+    conv = int((st == 0).sum())
+    del ws
+    # each shape class on its own (256 samples of one shape per call)
+    per_class = {}
+    for (P, Q), idx in sorted(by_shape.items()):
+        pq = PQ[idx]
+        ws1 = torch.empty(msg.msg_workspace_bytes(pq, prm), dtype=torch.uint8, device=dev)
+        Zi = torch.cat([Z[int(foff[i]):int(foff[i + 1])] for i in idx])
+        nq1 = len(idx) * P * Q
+        Q1, s1 = torch.empty(nq1, dtype=torch.float64, device=dev), torch.empty(len(idx), dtype=torch.int32, device=dev)
+        msg.msg_solve_batch(pq, prm, Zi, Q1, s1, None, None, ws1)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        msg.msg_solve_batch(pq, prm, Zi, Q1, s1, None, None, ws1)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        tc = f0.elapsed_time(f1) / 1000.0
+        per_class[f"{1 << P}x{1 << Q}"] = {"samples_per_s": round(int((s1 == 0).sum()) / tc, 1),
+                                          "converged": int((s1 == 0).sum())}
+        del ws1, Zi
+    # oracle check on fields the oracle builds itself (the GPU solves the same fields)
+    check_shapes = [(9, 3), (2, 9), (6, 6), (4, 7)]
+    Zo = []
+    for k, (P, Q) in enumerate(check_shapes):
+        Phi, sl = inputs.kl_basis(P, Q, law)
+        Zo.append(oracle.kl_field(Phi, sl, oracle.normals(seed + 1, k, M)))
+    inputs.kl_basis.cache_clear()
+    res = oracle.solve_batch(check_shapes, Zo, oracle.SolverParams(eps=1e-12, max_cycles=600, omega=a.omega))
+    Qg, sg, _, _ = msg.solve(np.array(check_shapes, dtype=np.int32), torch.from_numpy(np.concatenate(Zo)).to(dev), prm)
+    Qg = Qg.cpu().numpy()
+    off, errs = 0, []
+    for (P, Q), r in zip(check_shapes, res):
+        errs.append(float(np.max(np.abs(Qg[off:off + P * Q] - r[0].ravel()) / np.abs(r[0].ravel()))))
+        off += P * Q
+    line = {
+        "metric": "MSG samples/s, uneven index set", "value": conv * a.steps / t, "unit": "samples/s", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t / a.steps, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"uneven batch: {S} samples, 256 per index (a1,a2) in 0..7^2, grids 2^(a1+2) x "
+                               f"2^(a2+2) (4..512 per side), shuffled, one call; Matern nu=1.5 corr 0.2/0.02, KL "
+                               f"M={M} FP32; W(2,2) FMSG to eps={a.eps:g}", "S": S, "converged_fraction": conv / S},
+        "gpu_launches_per_step": launches / a.steps,
+        "per_shape_class_alone": per_class,
+        "oracle_check": {"shapes": [f"{1 << P}x{1 << Q}" for P, Q in check_shapes], "max_rel_err": errs,
+                         "gpu_status": sg.cpu().numpy().tolist()},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ serving workload --
+
+def serving_workload(a):
+    """The adaptive MSG-MIMC driver (Algorithm 3) feeding the continuous-batching
+    server with Poisson arrivals, for each tolerance of a sweep; samples/s and the
+    arrival-to-result latency percentiles."""
+    from paper_1907_12334_gb300 import msg
+    from paper_1907_12334_gb300.serving import MimcDriver, Server, run_driver
+
+    out = []
+    for eps, rate, cap in [(1e-2, 400.0, 3000), (3e-3, 800.0, 6000), (1e-3, 1600.0, 12000)]:
+        prm = msg.SolverParams(eps=1e-10, max_cycles=a.max_cycles, omega=a.omega)
+        srv = Server(hbm_budget_bytes=40 << 30, max_batch=512, slots=3, M=64, seed=7, prm=prm, p0=2, q0=2)
+        drv = MimcDriver(eps=eps, p0=2, q0=2, lmax=(8, 8), seed=5)
+        drv, results, wall = run_driver(srv, drv, rate_hz=rate, max_samples=cap, seed=9)
+        done = [r for r in results if r.status == 0]
+        lat = Server.latency_stats(done) if done else {}
+        out.append({"eps": eps, "rate_hz": rate, "samples": len(results), "ok": len(done),
+                    "samples_per_s": len(done) / wall, "wall_s": wall, "latency_ms": lat,
+                    "E": drv.E, "sqrt_V": float(np.sqrt(drv.V)), "rejected": srv.rejected,
+                    "failed_batches": len(srv.failures), "skipped": {k: sum(v.values()) for k, v in
+                                                                      drv.skipped_report().items()}})
+    line = {"metric": "served samples/s and p50/p99 latency", "value": out[-1]["samples_per_s"],
+            "unit": "samples/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "adaptive MSG-MIMC driver (Algorithm 3, geometric initial law) with Poisson "
+                                   "arrivals, tolerance sweep, indices up to (8,8) over base (2,2): grids up to "
+                                   "1024x1024; HBM budget 40 GiB; KL M=64"},
+            "sweep": out}
+    print(json.dumps(line), flush=True)
+
+
 def build_id():
     import hashlib
 
@@ -538,6 +772,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         reference_arm(a, rank, world)
+        return
+    if a.workload in ("kl", "uneven", "serving"):
+        if rank == 0:
+            {"kl": kl_workload, "uneven": uneven_workload, "serving": serving_workload}[a.workload](a)
         return
     if world > 1:
         import torch

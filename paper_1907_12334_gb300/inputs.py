@@ -135,6 +135,28 @@ def kl_basis(P: int, Q: int, law: FieldLaw = FieldLaw()):
     return Phi, sl
 
 
+def kl_basis_nodes(nx: int, ny: int, law: FieldLaw = FieldLaw(), rows=None):
+    """(Phi [len(rows) * nx][M] float64, sqrt_lambda [M]) at the nodes (i/(nx-1), j/(ny-1))
+    of an nx x ny grid, x fastest; `rows` (default all) selects the j of the returned
+    rows so that large grids can be built in pieces."""
+    nqx, nqy, lam, phi_q = _nystrom(law)
+    rows = np.arange(ny) if rows is None else np.asarray(rows)
+
+    def weights(f, nq):
+        t = np.clip(f * nq - 0.5, 0.0, nq - 1.0)
+        i0 = np.minimum(np.floor(t).astype(np.int64), nq - 2) if nq > 1 else np.zeros_like(t, dtype=np.int64)
+        return i0, t - i0
+
+    ix, axw = weights(np.arange(nx) / (nx - 1), nqx)
+    iy, ayw = weights(rows / (ny - 1), nqy)
+    M = lam.size
+    Phi = np.empty((rows.size, nx, M), dtype=np.float64)
+    for k in range(rows.size):
+        rowv = (1.0 - ayw[k]) * phi_q[iy[k]] + ayw[k] * phi_q[iy[k] + 1]  # [nqx][M]
+        Phi[k] = (1.0 - axw)[:, None] * rowv[ix] + axw[:, None] * rowv[ix + 1]
+    return Phi.reshape(rows.size * nx, M), np.sqrt(lam)
+
+
 def small_law(M: int = 32) -> FieldLaw:
     """The default law truncated to M terms (cheap set-up for small test cases)."""
     return FieldLaw(M=M)

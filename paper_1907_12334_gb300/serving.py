@@ -64,6 +64,8 @@ class MimcDriver:
         self.cnt = np.zeros((n1, n2))
         self.skipped: dict[str, np.ndarray] = {}  # reason -> per-index count of samples without a Y
         self.cost = np.array([[2.0 ** ((self.p0 + a) + (self.q0 + b)) for b in range(n2)] for a in range(n1)])
+        self.csum = np.zeros((n1, n2))  # measured work of the solves drawn at each index
+        self.ccnt = np.zeros((n1, n2))
 
     def pmf(self):
         """pi_L from the tail probabilities: P(L = l) by inclusion-exclusion."""
@@ -81,9 +83,13 @@ class MimcDriver:
     def shape(self, L):
         return (self.p0 + L[0], self.q0 + L[1])
 
-    def record(self, L, dQ, ptau_used):
-        """dQ: [(L1+1), (L2+1)] differences of one sample; ptau_used: the p_tau at draw time."""
+    def record(self, L, dQ, ptau_used, cost=None):
+        """dQ: [(L1+1), (L2+1)] differences of one sample; ptau_used: the p_tau at draw time;
+        cost: the measured work of the sample's solve (replaces the prior C_l of its index)."""
         Y = float((dQ / ptau_used[: L[0] + 1, : L[1] + 1]).sum())
+        if cost is not None and cost > 0:
+            self.csum[L[0], L[1]] += cost
+            self.ccnt[L[0], L[1]] += 1
         self.n += 1
         self.Ysum += Y
         self.Y2sum += Y * Y
@@ -98,7 +104,7 @@ class MimcDriver:
     def take(self, req):
         """Fold one finished request into the estimator (record) or the skip counts."""
         if req.status == 0 and req.dQ is not None:
-            return self.record(req.L, req.dQ, req.ptau)
+            return self.record(req.L, req.dQ, req.ptau, req.cost or None)
         self.skip(req.L, req.status)
         return None
 
@@ -128,7 +134,15 @@ class MimcDriver:
         ok = self.cnt >= 8
         if not ok[0, 0]:
             return
-        w = np.where(ok, np.sqrt(np.maximum(v, 0) / self.cost), 0.0)
+        # C_l: measured mean work where solves at that index have been timed, else the prior
+        # 2^(p+q) rescaled to the measured ones (Algorithm 3 updates pi_L from estimates)
+        cost = self.cost.copy()
+        seen = self.ccnt > 0
+        if seen.any():
+            mc = self.csum[seen] / self.ccnt[seen]
+            scale = float(np.exp(np.mean(np.log(mc / self.cost[seen]))))
+            cost = np.where(seen, self.csum / np.maximum(self.ccnt, 1), self.cost * scale)
+        w = np.where(ok, np.sqrt(np.maximum(v, 0) / cost), 0.0)
         if w[0, 0] <= 0:
             return
         t = w / w[0, 0]
@@ -153,6 +167,16 @@ class MimcDriver:
         return self.n >= 2 and math.sqrt(self.V) <= self.eps
 
 
+def measured_cost(cycles):
+    """Work of one FMSG solve from the cycles each grid used: a mu-cycle of Algorithm 1
+    with grid (p,q) as its top visits every grid of its hierarchy about once per
+    finest-grid unknown (Sec. 2), so a cycle costs ~ p q 2^(p+q) unknown updates."""
+    P, Q = cycles.shape
+    p = np.arange(1, P + 1)[:, None]
+    q = np.arange(1, Q + 1)[None, :]
+    return float((cycles * p * q * np.exp2(p + q)).sum())
+
+
 # ------------------------------------------------------------------ server --
 
 STATUS_REFUSED = -1       # request larger than the whole HBM budget
@@ -171,6 +195,7 @@ class Request:
     dQ: np.ndarray | None = None
     status: int = 0  # MSG_SAMPLE_* bits of the solve, or STATUS_REFUSED / STATUS_BATCH_FAILED
     error: str = ""
+    cost: float = 0.0  # measured work of the solve (see measured_cost)
 
 
 class Server:
@@ -238,29 +263,38 @@ class Server:
                 shapes = np.array([r.shape for r in reqs], dtype=np.int32)
                 nq, nf = msg.packed_sizes(shapes)
                 Z = torch.empty(nf, dtype=torch.float64, device=self.dev)
-                off = 0
-                # fields: group by shape so each KL contraction uses one basis
-                xi = torch.empty((1, self.M), dtype=torch.float64, device=self.dev)
-                for r in reqs:
-                    prep, npts = self.basis(*r.shape)
-                    msg.msg_normals(self.seed, r.sample, 1, self.M, xi, stream=st)
-                    msg.sample_field(prep, npts, self.M, msg.MSG_GEMM_FP64, xi, Z[off:off + npts], stream=st)
-                    off += npts
+                foff = np.concatenate([[0], np.cumsum([msg.field_points(*r.shape) for r in reqs])])
+                # fields: one KL contraction per shape group of the batch (each group's basis
+                # stays on the device), then placed at the requests' offsets
+                groups = {}
+                for k, r in enumerate(reqs):
+                    groups.setdefault(tuple(r.shape), []).append(k)
+                for shape, ks in groups.items():
+                    prep, npts = self.basis(*shape)
+                    xi = torch.empty((len(ks), self.M), dtype=torch.float64, device=self.dev)
+                    for j, k in enumerate(ks):
+                        msg.msg_normals(self.seed, reqs[k].sample, 1, self.M, xi[j:j + 1], stream=st)
+                    Zs = torch.empty((len(ks), npts), dtype=torch.float64, device=self.dev)
+                    msg.sample_field(prep, npts, self.M, msg.MSG_GEMM_FP64, xi, Zs, stream=st)
+                    for j, k in enumerate(ks):
+                        Z[int(foff[k]):int(foff[k + 1])].copy_(Zs[j])
                 Q = torch.empty(nq, dtype=torch.float64, device=self.dev)
                 status = torch.empty(S, dtype=torch.int32, device=self.dev)
+                cyc = torch.empty(nq, dtype=torch.int32, device=self.dev)
                 ws = torch.empty(msg.msg_workspace_bytes(shapes, self.prm), dtype=torch.uint8, device=self.dev)
-                msg.msg_solve_batch(shapes, self.prm, Z, Q, status, workspace=ws, stream=st)
+                msg.msg_solve_batch(shapes, self.prm, Z, Q, status, cycles=cyc, workspace=ws, stream=st)
                 Ls = np.array([r.L for r in reqs], dtype=np.int32)
                 nd = int(sum((a + 1) * (b + 1) for a, b in Ls))
                 dQ = torch.empty(nd, dtype=torch.float64, device=self.dev)
                 msg.mimc_differences(Ls, self.p0, self.q0, Q, dQ, stream=st)
                 st.synchronize()
-                Qh, dQh, sth = Q.cpu().numpy(), dQ.cpu().numpy(), status.cpu().numpy()
+                Qh, dQh, sth, cych = Q.cpu().numpy(), dQ.cpu().numpy(), status.cpu().numpy(), cyc.cpu().numpy()
             t = time.perf_counter()
             oq = od = 0
             for k, r in enumerate(reqs):
                 P, Qn = r.shape
                 r.Q = Qh[oq:oq + P * Qn].reshape(P, Qn)
+                r.cost = measured_cost(cych[oq:oq + P * Qn].reshape(P, Qn))
                 oq += P * Qn
                 a, b = r.L[0] + 1, r.L[1] + 1
                 r.dQ = dQh[od:od + a * b].reshape(a, b)

@@ -175,3 +175,26 @@ def test_served_results_match_the_oracle():
         np.testing.assert_allclose(got.dQ, dQo, rtol=0, atol=1e-8 * np.abs(Qo).max())
         checked += 1
     assert checked >= 0.9 * len(reqs)
+
+
+def test_measured_cost_and_learned_law_use_it():
+    """The measured work of a solve weights each grid's cycles by the W-cycle work of
+    that grid as top (p q 2^(p+q)); once solves at an index are timed, Algorithm 3's
+    update uses their mean measured cost in place of the 2^(p+q) prior."""
+    from paper_1907_12334_gb300.serving import measured_cost
+
+    cyc = np.array([[1, 2], [3, 4]])
+    assert measured_cost(cyc) == 1 * 1 * 1 * 4 + 2 * 1 * 2 * 8 + 3 * 2 * 1 * 8 + 4 * 2 * 2 * 16
+    rng = np.random.default_rng(1)
+    a = MimcDriver(eps=1e-6, lmax=(2, 2), learn_every=10**9)
+    b = MimcDriver(eps=1e-6, lmax=(2, 2), learn_every=10**9)
+    for L in a.draw(3000):
+        dq = rng.standard_normal((L[0] + 1, L[1] + 1)) * 0.5 ** np.add.outer(np.arange(L[0] + 1), np.arange(L[1] + 1))
+        a.record(L, dq, a.tail)
+        # index (1, 1) measured 64x more expensive than the prior says, the others as the prior
+        c = b.cost[L[0], L[1]] * (64.0 if L == (1, 1) else 1.0)
+        b.record(L, dq, b.tail, cost=c)
+    a.learn()
+    b.learn()
+    assert b.tail[1, 1] < a.tail[1, 1]  # the costlier index is drawn less often
+    assert b.tail[0, 0] == a.tail[0, 0] == 1.0
