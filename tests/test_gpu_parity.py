@@ -200,8 +200,8 @@ def test_launch_shapes_do_not_change_results(msg, shape):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("cut", [1, 3, 5])
-def test_low_kernel_cut_changes_rounding_only(msg, cut):
+@pytest.mark.parametrize("cut,shape", [(1, {}), (3, {}), (5, dict(tune_low_items=1, tune_low_warps=8))])
+def test_low_kernel_cut_changes_rounding_only(msg, cut, shape):
     """The diagonal up to which the low-diagonal kernel runs the recursion (the rest
     are separate visit launches) changes only the rounding of the FP32 cycles: every
     grid still meets eps and the QoIs agree with the default cut and with the oracle
@@ -209,7 +209,7 @@ def test_low_kernel_cut_changes_rounding_only(msg, cut):
     shapes = SHAPES_SMALL + [(2, 6), (6, 2), (5, 4), (6, 6)]
     Zs = oracle_fields(shapes, seed=8)
     ref = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300)
-    got = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300, tune_low_cut=cut)
+    got = run_gpu(msg, shapes, Zs, eps=1e-10, max_cycles=300, tune_low_cut=cut, **shape)
     assert np.array_equal(ref[1], got[1]) and (got[1] == 0).all()
     assert np.all(got[3] <= 1e-10)
     np.testing.assert_allclose(got[0], ref[0], rtol=1e-8)
