@@ -12,11 +12,13 @@
 // Z[s][x] = sum_m A[s][m] B[x][m] with A = sqrt(lambda) * xi (samples x terms)
 // and B = Phi (points x terms).  One CTA computes a 128 (samples) x 256 (points)
 // tile of Z: accumulators in 256 TMEM columns, K in 128-byte chunks (64 bf16 or
-// 32 TF32 terms) staged through two shared-memory stages in the 128-byte-swizzled
-// K-major layout the UMMA descriptors expect.  A is converted on the fly from FP64
-// xi and sqrt(lambda); B is converted once by kl_tc_prepare into zero-padded
-// [Np][Kp] part arrays and its tiles arrive by 16-byte asynchronous copies
-// (cp.async) while the A chunk is being converted.  One elected thread issues the
+// 32 TF32 terms) staged through shared memory in the 128-byte-swizzled K-major
+// layout the UMMA descriptors expect.  A is converted from FP64
+// xi and sqrt(lambda) once per call into a stream-ordered temporary; B is
+// converted once per basis by kl_tc_prepare; both are zero-padded [rows][Kp] part
+// arrays whose tiles arrive by 16-byte asynchronous copies (cp.async) through a
+// ring of stages (2 for BF16X3, 4 for TF32) filled ahead of the MMAs that read
+// them.  One elected thread issues the
 // MMAs and commits them to an mbarrier per stage; every wait is bounded and a
 // timeout sets a device flag (read by msg_device_status) instead of hanging.  The
 // epilogue moves each warp's 32 x 32 accumulator blocks through shared memory so
@@ -44,16 +46,18 @@ enum { TC_BF16X3 = 0, TC_TF32 = 1 };
 template <int MODE> struct TcCfg;
 template <> struct TcCfg<TC_BF16X3> {
     typedef __nv_bfloat16 E;
-    static constexpr int parts = 2;  // hi, lo
-    static constexpr int TK = 64;    // terms per 128-byte row
+    static constexpr int parts = 2;   // hi, lo
+    static constexpr int TK = 64;     // terms per 128-byte row
+    static constexpr int stages = 2;  // 96 KB each
 };
 template <> struct TcCfg<TC_TF32> {
     typedef float E;
     static constexpr int parts = 1;
     static constexpr int TK = 32;
+    static constexpr int stages = 4;  // 48 KB each
 };
 template <int MODE> constexpr int stage_bytes() { return TcCfg<MODE>::parts * (kAbytes + kBbytes); }
-template <int MODE> constexpr int smem_bytes() { return 2 * stage_bytes<MODE>() + 1024; }  // + alignment slack
+template <int MODE> constexpr int smem_bytes() { return TcCfg<MODE>::stages * stage_bytes<MODE>() + 1024; }  // + alignment slack
 
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -191,6 +195,27 @@ __global__ void k_tf32_phi(const double* Phi, int64_t npts, int M, int64_t Kp, i
     }
 }
 
+// A = sqrt(lambda) * xi converted once per call into zero-padded [Sp][Kp] part
+// arrays in the operand format (the main loop then only copies).
+template <int MODE>
+__global__ void k_prep_a(const double* sl, const double* xi, int64_t S, int M, int64_t Kp, int64_t Sp,
+                         typename TcCfg<MODE>::E* A0, typename TcCfg<MODE>::E* A1)
+{
+    const int64_t n = Sp * Kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / Kp, m = e % Kp;
+        const double v = (s < S && m < M) ? sl[m] * xi[s * M + m] : 0.0;
+        if constexpr (MODE == TC_TF32) {
+            A0[e] = to_tf32(v);
+        } else {
+            __nv_bfloat16 h, l;
+            split2(v, h, l);
+            A0[e] = h;
+            A1[e] = l;
+        }
+    }
+}
+
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -198,14 +223,15 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 
 template <int MODE, class TZ>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_kl_tc(const typename TcCfg<MODE>::E* __restrict__ B0, const typename TcCfg<MODE>::E* __restrict__ B1,
-            const double* __restrict__ sl, const double* __restrict__ xi, int64_t npts, int M, int64_t Kp, int64_t S,
-            TZ* __restrict__ Z)
+    k_kl_tc(const typename TcCfg<MODE>::E* __restrict__ A0, const typename TcCfg<MODE>::E* __restrict__ A1,
+            const typename TcCfg<MODE>::E* __restrict__ B0, const typename TcCfg<MODE>::E* __restrict__ B1,
+            int64_t npts, int64_t Kp, int64_t S, TZ* __restrict__ Z)
 {
     typedef typename TcCfg<MODE>::E E;
-    constexpr int parts = TcCfg<MODE>::parts, TK = TcCfg<MODE>::TK, EPC = 16 / (int)sizeof(E);  // terms per chunk
+    constexpr int parts = TcCfg<MODE>::parts, TK = TcCfg<MODE>::TK, NST = TcCfg<MODE>::stages;
+    constexpr int EPC = 16 / (int)sizeof(E);  // terms per 16-byte chunk
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[NST];
     __shared__ uint32_t tmem_base_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // 1024-aligned stage buffers (swizzle atoms must start on 1024 bytes)
@@ -220,8 +246,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int k = 0; k < NST; ++k) mbar_init(&bars[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -230,13 +255,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const uint32_t tmem = tmem_base_slot;
 
     const int nchunks = (int)(Kp / TK);
-    bool ok = true;
-    for (int kc = 0; kc < nchunks; ++kc) {
-        const int st = kc & 1;
-        unsigned char* sA = base + st * stage_bytes<MODE>();  // A parts, then B parts
+    // one chunk of A (128 rows) and B (256 rows) into its stage by 16-byte asynchronous copies
+    auto load_chunk = [&](int kc) {
+        unsigned char* sA = base + (kc % NST) * stage_bytes<MODE>();  // A parts, then B parts
         unsigned char* sB = sA + parts * kAbytes;
-        if (kc >= 2) ok &= mbar_wait(&bars[st], ((kc >> 1) - 1) & 1);  // the MMAs that read this stage are done
-        // B chunk: 256 rows x 8 chunks per part, already converted and zero padded
+        for (int t = tid; t < kTM * 8; t += kThreadsTC) {
+            const int r = t >> 3, c = t & 7;
+            const int64_t g = (s0 + r) * Kp + (int64_t)kc * TK + c * EPC;
+            const uint32_t off = sw128(r, c);
+            cp_async16(smem_u32(sA + off), A0 + g);
+            if constexpr (parts == 2) cp_async16(smem_u32(sA + kAbytes + off), A1 + g);
+        }
         for (int t = tid; t < kTN * 8; t += kThreadsTC) {
             const int r = t >> 3, c = t & 7;
             const int64_t g = (x0 + r) * Kp + (int64_t)kc * TK + c * EPC;
@@ -244,54 +273,45 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             cp_async16(smem_u32(sB + off), B0 + g);
             if constexpr (parts == 2) cp_async16(smem_u32(sB + kBbytes + off), B1 + g);
         }
+    };
+    // prologue: the first NST-1 chunks in flight (one commit group per chunk, empty past the end)
+    for (int kc = 0; kc < NST - 1; ++kc) {
+        if (kc < nchunks) load_chunk(kc);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        // A chunk: 128 rows x 8 chunks, converted on the fly while B is in flight
-        for (int t = tid; t < kTM * 8; t += kThreadsTC) {
-            const int r = t >> 3, c = t & 7;
-            const int64_t s = s0 + r;
-            const uint32_t off = sw128(r, c);
-            if constexpr (MODE == TC_BF16X3) {
-                __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int m = kc * TK + c * 8 + j;
-                    double v = (s < S && m < M) ? sl[m] * xi[s * M + m] : 0.0;
-                    split2(v, h[j], l[j]);
-                }
-                *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(h);
-                *reinterpret_cast<uint4*>(sA + kAbytes + off) = *reinterpret_cast<const uint4*>(l);
-            } else {
-                __align__(16) float f[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int m = kc * TK + c * 4 + j;
-                    f[j] = (s < S && m < M) ? to_tf32(sl[m] * xi[s * M + m]) : 0.f;
-                }
-                *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(f);
-            }
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make the stores visible to the tensor cores
+    }
+    bool ok = true;
+    for (int kc = 0; kc < nchunks; ++kc) {
+        // chunk kc has landed once at most NST-2 newer groups are pending
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make the copies visible to the tensor cores
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t a0 = smem_u32(base + (kc % NST) * stage_bytes<MODE>());
+            const uint32_t b0 = a0 + parts * kAbytes;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {  // 4 MMA K steps of 32 bytes per 128-byte row
                 const uint32_t ko = ks * 32;
                 const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
                 mma<MODE>(tmem, smem_desc(a0 + ko), smem_desc(b0 + ko), first);
                 if constexpr (MODE == TC_BF16X3) {
-                    mma<MODE>(tmem, smem_desc(a0 + ko), smem_desc(b0 + kBbytes + ko), 1u);            // hi * lo
-                    mma<MODE>(tmem, smem_desc(a0 + kAbytes + ko), smem_desc(b0 + ko), 1u);            // lo * hi
+                    mma<MODE>(tmem, smem_desc(a0 + ko), smem_desc(b0 + kBbytes + ko), 1u);  // hi * lo
+                    mma<MODE>(tmem, smem_desc(a0 + kAbytes + ko), smem_desc(b0 + ko), 1u);  // lo * hi
                 }
             }
-            mma_commit(&bars[st]);
+            mma_commit(&bars[kc % NST]);
         }
+        // refill: chunk kc+NST-1 goes into the stage chunk kc-1 used, once its MMAs are done
+        const int nk = kc + NST - 1;
+        if (nk < nchunks) {
+            if (kc >= 1) ok &= mbar_wait(&bars[(kc - 1) % NST], ((kc - 1) / NST) & 1);
+            load_chunk(nk);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    // wait for the last one or two stages' MMAs
-    if (nchunks >= 2) ok &= mbar_wait(&bars[(nchunks - 2) & 1], ((nchunks - 2) >> 1) & 1);
-    if (nchunks >= 1) ok &= mbar_wait(&bars[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+    // the last commit completes after every MMA of the CTA
+    if (nchunks >= 1) ok &= mbar_wait(&bars[(nchunks - 1) % NST], ((nchunks - 1) / NST) & 1);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // every thread took part in the same waits; make the decision CTA-wide
     const int all_ok = __syncthreads_and(ok ? 1 : 0);
@@ -349,11 +369,23 @@ int tc_launch(const TcLayout& L, const char* b, int64_t npts, int32_t M, const d
               cudaStream_t st)
 {
     typedef typename TcCfg<MODE>::E E;
-    dim3 grid((unsigned)(L.Np / kTN), (unsigned)((S + kTM - 1) / kTM));
+    constexpr int parts = TcCfg<MODE>::parts;
+    const int64_t Sp = round_up(S, kTM);
+    const size_t apart = (size_t)Sp * L.Kp * sizeof(E), apart_al = (apart + 255) / 256 * 256;
+    // the converted A lives in a stream-ordered temporary, freed after the contraction
+    char* abuf = nullptr;
+    MSG_CUDA_TRY(cudaMallocAsync((void**)&abuf, parts * apart_al, st));
+    E* A0 = (E*)abuf;
+    E* A1 = parts == 2 ? (E*)(abuf + apart_al) : nullptr;
+    k_prep_a<MODE><<<152 * 4, 256, 0, st>>>((const double*)(b + L.sl), xi, S, M, L.Kp, Sp, A0, A1);
+    MSG_CHECK_LAUNCH();
+    dim3 grid((unsigned)(L.Np / kTN), (unsigned)(Sp / kTM));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<MODE>()));
-    k_kl_tc<MODE, TZ><<<grid, kThreadsTC, smem_bytes<MODE>(), st>>>((const E*)(b + L.p0), (const E*)(b + L.p1),
-                                                                     (const double*)(b + L.sl), xi, npts, M, L.Kp, S,
-                                                                     (TZ*)Z);
+    k_kl_tc<MODE, TZ><<<grid, kThreadsTC, smem_bytes<MODE>(), st>>>(A0, A1 ? A1 : A0, (const E*)(b + L.p0),
+                                                                     (const E*)(b + (parts == 2 ? L.p1 : L.p0)), npts,
+                                                                     L.Kp, S, (TZ*)Z);
+    MSG_CHECK_LAUNCH();
+    MSG_CUDA_TRY(cudaFreeAsync(abuf, st));
     return MSG_OK;
 }
 
