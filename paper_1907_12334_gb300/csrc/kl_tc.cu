@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // 1024-aligned stage buffers (swizzle atoms must start on 1024 bytes)
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char* base = smem_raw + (((raw + 1023) & ~1023u) - raw);
-    const int64_t s0 = (int64_t)blockIdx.y * kTM, x0 = (int64_t)blockIdx.x * kTN;
+    // blockIdx.x runs over the sample tiles: the CTAs that read one Phi tile are
+    // launched next to each other and find it in L2 (A is small and stays there)
+    const int64_t s0 = (int64_t)blockIdx.x * kTM, x0 = (int64_t)blockIdx.y * kTN;
 
     if (warp == 0) {  // TMEM: 128 lanes x 256 FP32 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
@@ -379,7 +381,7 @@ int tc_launch(const TcLayout& L, const char* b, int64_t npts, int32_t M, const d
     E* A1 = parts == 2 ? (E*)(abuf + apart_al) : nullptr;
     k_prep_a<MODE><<<152 * 4, 256, 0, st>>>((const double*)(b + L.sl), xi, S, M, L.Kp, Sp, A0, A1);
     MSG_CHECK_LAUNCH();
-    dim3 grid((unsigned)(L.Np / kTN), (unsigned)(Sp / kTM));
+    dim3 grid((unsigned)(Sp / kTM), (unsigned)(L.Np / kTN));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_kl_tc<MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<MODE>()));
     k_kl_tc<MODE, TZ><<<grid, kThreadsTC, smem_bytes<MODE>(), st>>>(A0, A1 ? A1 : A0, (const E*)(b + L.p0),
                                                                      (const E*)(b + (parts == 2 ? L.p1 : L.p0)), npts,
@@ -416,7 +418,7 @@ int32_t kl_tc_sample(const void* prepared, int64_t npts, int32_t M, int32_t mode
 {
     const int tm = tc_mode(mode);
     const TcLayout L = tc_layout(npts, M, tm);
-    if ((S + kTM - 1) / kTM > 65535) { set_error("sample_field: too many samples for one call"); return MSG_ERR_INVALID; }
+    if ((npts + kTN - 1) / kTN > 65535) { set_error("sample_field: too many points for one call"); return MSG_ERR_INVALID; }
     const char* b = (const char*)prepared;
     prof_begin(K_KL, st);
     int rc;
