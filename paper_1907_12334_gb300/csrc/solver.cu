@@ -1447,7 +1447,18 @@ struct LowShape {
     int warps;  // warps per CTA
     int pcap[kLowMax + 1], ecap[kLowMax + 1];  // program words / entries of the largest class of each dl
     size_t smem[kLowMax + 1];                  // bytes per CTA of a launch at each dl
+    double flops[kLowClassesMax];              // algorithmic FP operations of one mu-cycle of each class
 };
+
+// Algorithmic floating-point operations of one node entry of each phase kind
+// (a reciprocal counts as one): smoothing 4 mul + 3 add for the neighbours, 3 add
+// for the diagonal, rcp, add b, mul = 13; residual 4 + 3 + 3 + 1 mul + 2 sub +
+// 1 sub = 14; restriction 2 x (2 add + 1 mul + 1 mul) + 3 = 11; prolongation
+// 2 x (add + mul) + kappa (2 add, 2 mul, add, rcp, 2 mul) + 2 mul + add + fma = 16.
+static double low_kind_flops(int kind)
+{
+    return kind <= LK_BLACK ? 13.0 : kind == LK_RESID ? 14.0 : kind == LK_RESTRICT ? 11.0 : 16.0;
+}
 static LowShape low_shape_at(const msg_params& prm, int cut, int items, int warps)
 {
     const size_t es = prm.precision == MSG_PREC_MIXED ? sizeof(float) : sizeof(double);
@@ -1468,6 +1479,18 @@ static LowShape low_shape_at(const msg_params& prm, int cut, int items, int warp
         s.pcap[dl] = (s.pcap[dl] + 1) & ~1;  // whole 16-byte chunks: the planes after it start 16-byte aligned
         s.smem[dl] = sizeof(uint4) * s.ecap[dl] + sizeof(uint2) * s.pcap[dl] +
                      es * (size_t)low_stride(lt.planes[dl], items, es) * items * warps;
+    }
+    // work of one mu-cycle per class, counted on the all-table program (the register
+    // path below diagonal 3 does the same node updates)
+    std::vector<LowDesc> dt;
+    const std::vector<uint2> rpt = low_resolve(prm, dt, false);
+    for (int c = 0; c < kLowClassesMax; ++c) {
+        double f = 0.0;
+        for (int o = 0; o < dt[c].nops; ++o) {
+            const uint2 w = rpt[dt[c].prog + o];
+            f += (double)(w.x >> 3) * low_kind_flops((int)(w.x & 7));
+        }
+        s.flops[c] = f;
     }
     return s;
 }
@@ -1806,7 +1829,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
     std::vector<size_t> dseg0(L + 1, 0), dnseg(L + 1, 0);
     std::vector<double> dpre(L + 1, 0), dpost(L + 1, 0);
     int64_t nitems = 0;
-    double item_pts = 0, low_bytes = 0;
+    double item_pts = 0, low_bytes = 0, low_flops = 0;
     // Upload per-item sample lists and segments for `lists` (item level first,
     // then one list per diagonal above the warp cut when with_diag).
     auto build_lists = [&](const std::vector<std::vector<int>>& lists, bool with_diag) -> int {
@@ -1834,9 +1857,11 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             // warp tasks of the low-diagonal kernel: up to KW items of one segment (one class) each
             // (the warps of a CTA take tasks of one segment: idle warps pad each segment's last CTA)
             ntasks = 0;
+            low_flops = 0;
             for (size_t k = 0; k < ns; ++k) {
                 const Segment& sgk = h_segs[k];
                 const int cls = low_class(std::min(sgk.pi, dl + 1), std::min(sgk.qi, dl + 1), dl);
+                low_flops += (double)sgk.count * C.low.flops[cls];
                 for (int64_t f = 0; f < sgk.count; f += C.low.items)
                     h_tasks[ntasks++] = LowTask{(int)k, (int)f, (int)std::min<int64_t>(C.low.items, sgk.count - f), cls};
                 while (ntasks % C.low.warps) h_tasks[ntasks++] = LowTask{(int)k, 0, 0, cls};
@@ -2025,7 +2050,7 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             default: k_lowv<T, 8><<<nb, 32 * wpb, smem, st>>>(ic, dtasks, su, sbx, sby, img, istr, ify, C.low_desc, C.low_ent,
                                                              C.low_prog, lp, stride, pc, ec, calls, om); break;
             }
-            prof_end(K_LOW, st, low_bytes, 0.0, d);
+            prof_end(K_LOW, st, low_bytes, low_flops * calls, d);
             launch_err |= cudaGetLastError() != cudaSuccess;
         };
         auto launch_half = [&](int d, int pre, int zi) {
