@@ -926,7 +926,10 @@ __global__ void __launch_bounds__(32 * kLowWarpsMax) k_lowv(DevCtx cx, const Low
             const uint2 op = sprog[o];
             const int kind = op.x & 7, cnt = (int)(op.x >> 3), off = (int)op.y;
             if (kind == LK_CALL2) {
-                if (act && el == 0) low_call2(D.pic, D.qic, u, b, fx, fy, cp.mu, cp.nu1, cp.nu2, omega);
+                // FP32 only: the FP64 programs are built without this phase (the register path
+                // would not fit beside the kernel's FP64 state)
+                if constexpr (std::is_same<T, float>::value)
+                    if (act && el == 0) low_call2(D.pic, D.qic, u, b, fx, fy, cp.mu, cp.nu1, cp.nu2, omega);
             } else if (act) {
                 // entries of one phase are independent: four per lane in flight at a time
                 // (a lane's last group repeats its first entry where it has fewer than four)
@@ -1417,6 +1420,7 @@ static std::vector<int> low_program(int dl, const msg_params& prm, bool reg2)
 // restriction is empty.
 static std::vector<uint2> low_resolve(const msg_params& prm, std::vector<LowDesc>& desc, bool reg2 = true)
 {
+    reg2 = reg2 && prm.precision == MSG_PREC_MIXED;  // the register path is built for FP32 cycles
     desc = low_tables().desc;
     std::vector<int> words[kLowMax + 1];
     for (int dl = 0; dl <= kLowMax; ++dl) words[dl] = low_program(dl, prm, reg2);

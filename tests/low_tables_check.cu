@@ -152,7 +152,7 @@ static int check_program()
     for (int qic = 1; qic <= dl + 1; ++qic) {
         if (pic + qic < dl + 2) continue;  // no item has such a class
         if (dl == kLowMax && mu == 3) continue;  // keeps the host run short; mu = 3 is covered below kLowMax
-        msg_params prm{}; prm.mu = mu; prm.nu1 = nu; prm.nu2 = nu; prm.omega = 1.0;
+        msg_params prm{}; prm.mu = mu; prm.nu1 = nu; prm.nu2 = nu; prm.omega = 1.0; prm.precision = MSG_PREC_MIXED;
         std::vector<LowDesc> desc;
         std::vector<uint2> rp = low_resolve(prm, desc, reg2 != 0);
         const LowDesc& D = desc[low_class(pic, qic, dl)];
