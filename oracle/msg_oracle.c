@@ -544,9 +544,13 @@ static double grid_relres(ogrid* g)
  * residuals of one error), until its own ||r||/||b|| <= eps (at least one
  * cycle, at most max_cycles).  READING: the paper only says the cycle count is
  * increased until the criterion holds; a grid whose relative residual after
- * a cycle exceeds 1 (worse than the zero guess) has diverged and stops there,
- * flagged as not converged, instead of running on to max_cycles.  The solution of each grid is saved when its
- * stage ends, before cycles on finer diagonals reuse its u and b as scratch. */
+ * a cycle exceeds both 1 (the zero guess) and the relative residual of its
+ * initial guess has diverged and stops there, flagged as not converged,
+ * instead of running on to max_cycles.  (On strongly anisotropic grids the
+ * interpolated initial guess can start well above 1 and a converging grid may
+ * still be above 1 after its first cycle.)  The solution of each grid is saved
+ * when its stage ends, before cycles on finer diagonals reuse its u and b as
+ * scratch. */
 static void f_cycle(ohier* H, int s)
 {
     if (s == 0) {
@@ -563,11 +567,12 @@ static void f_cycle(ohier* H, int s)
         H->Pa = p; H->Qa = q; /* the hierarchy below (p,q) */
         int n = 0;
         double rr = 0.0;
+        const double rr0 = grid_relres(g); /* the initial guess */
         do {
             orc_mu_cycle(H, s);
             ++n;
             rr = grid_relres(g);
-        } while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && rr <= 1.0);
+        } while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && (rr <= 1.0 || rr <= rr0));
         H->Pa = H->P; H->Qa = H->Q;
         H->grid_cycles[(p - 1) * H->Q + (q - 1)] = n;
         H->grid_relres[(p - 1) * H->Q + (q - 1)] = rr;

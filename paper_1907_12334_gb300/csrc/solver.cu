@@ -1133,11 +1133,16 @@ __global__ void k_residual(DevCtx cx, const double* u64, const double* ax64, con
     if (threadIdx.x == 0) {
         const int step = nstep[t.item];  // cycles done on this item so far
         double rr = sqrt(ss / (double)n);  // ||b|| with b = 1 on n interior nodes
+        // diverged: worse than both the zero guess (1) and the item's initial guess, whose
+        // relative residual is kept in relres until the item finishes
         int act;
-        if (step == 0) act = 1;  // at least one cycle
+        if (step == 0) { act = 1; relres[t.item] = rr; }  // at least one cycle
         else if (!(rr == rr) || isinf(rr)) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NONFINITE); }
         else if (rr <= eps) act = 0;
-        else if (step >= max_cycles || rr > 1.0) { act = 0; atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED); }
+        else if (step >= max_cycles || (rr > 1.0 && rr > relres[t.item])) {
+            act = 0;
+            atomicOr(&status[t.s], MSG_SAMPLE_NOT_CONVERGED);
+        }
         else act = 1;
         sflag[t.sidx] = act;
         if (!act) {

@@ -38,6 +38,9 @@ MUTATIONS = [
      "double a = exp(Z[(int64_t)(2 * j * sy) * NFx + (NFx - 2)]);", "boundary_column"),
     ("flux boundary row", "double a = exp(Z[(int64_t)(2 * j * sy) * NFx + (NFx - 1)]);",
      "double a = exp(Z[(int64_t)(2 * j * sy + 1) * NFx + (NFx - 1)]);", "boundary_column"),
+    ("divergence against the zero guess only",
+     "while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && (rr <= 1.0 || rr <= rr0));",
+     "while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && rr <= 1.0);", "keeps_cycling"),
     ("box-muller radius", "double rad = sqrt(-2.0 * log(1.0 - ua));", "double rad = sqrt(-1.0 * log(1.0 - ua));",
      "normals_distribution"),
 ]

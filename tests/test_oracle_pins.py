@@ -419,6 +419,31 @@ def test_flux_qoi_reads_the_boundary_column_of_a_varying_field():
         assert H.qoi(p, q, qoi=oracle.QOI_FLUX) == pytest.approx(want, rel=1e-13), (p, q)
 
 
+def test_grid_above_the_zero_guess_after_one_cycle_keeps_cycling():
+    """Divergence reading: a grid stops as diverged only when a cycle leaves its
+    relative residual above both 1 (the zero guess) and its initial guess's.  On this
+    deterministic field (sharp variation along y, a 16 x 128 finest grid) the
+    interpolated initial guess of grid (3,4) starts far above 1 and is still above 1
+    after its first cycle; it must keep cycling, and every grid then meets eps and
+    agrees with a dense direct solve of its own system."""
+    P, Q = 4, 7
+    NFy, NFx = inputs.field_grid_shape(P, Q)
+    X, Y = np.meshgrid(np.arange(NFx) / (NFx - 1), np.arange(NFy) / (NFy - 1))
+    Z = (2.0 * np.sin(14 * np.pi * Y + 1.3) * np.cos(2 * np.pi * X) + np.sin(16 * np.pi * X * Y)).ravel()
+    prm = oracle.SolverParams(eps=1e-10, max_cycles=400)
+    Qg, st, cyc, rr = oracle.solve_sample(P, Q, Z, prm)
+    assert st == 0 and np.all(rr <= 1e-10)
+    assert cyc[2, 3] > 10  # the grid that a stop at 1 would have abandoned after one cycle
+    H = oracle.Hierarchy(P, Q, Z, prm)
+    st2, cyc2, _ = H.fmsg()
+    assert st2 == 0 and np.array_equal(cyc2, cyc)
+    for p, q in [(3, 4), (3, 5)]:
+        A = _dense(H, p, q)
+        u = np.linalg.solve(A, np.ones(A.shape[0]))
+        got = H.get(p, q, oracle.SOL)[1:-1, 1:-1].ravel()
+        assert np.max(np.abs(got - u)) <= 1e-6 * np.max(np.abs(u))
+
+
 # ------------------------------------------------------------------- MIMC --
 
 def test_mixed_difference_worked_example():
