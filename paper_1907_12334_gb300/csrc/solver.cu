@@ -1505,13 +1505,13 @@ static LowShape low_shape_at(const msg_params& prm, int cut, int items, int warp
 }
 // Defaults (the fastest measured at 256 x 256, S = 4096): cut 4 with two items
 // per warp and 16 warps per CTA for FP32 cycles, cut 4 with one item per warp
-// and 8 warps for FP64.  With long programs (large mu or nu) the default cut
+// and 16 warps for FP64.  With long programs (large mu or nu) the default cut
 // drops until the CTA fits the shared memory.
 static LowShape low_shape(const msg_params& prm)
 {
     const bool mixed = prm.precision == MSG_PREC_MIXED;
     const int items = prm.tune_low_items ? prm.tune_low_items : (mixed ? 2 : 1);
-    const int warps = prm.tune_low_warps ? prm.tune_low_warps : (mixed ? 16 : 8);
+    const int warps = prm.tune_low_warps ? prm.tune_low_warps : 16;
     if (prm.tune_low_cut) return low_shape_at(prm, prm.tune_low_cut, items, warps);
     for (int cut = 4; cut > 1; --cut) {
         LowShape s = low_shape_at(prm, cut, items, warps);
