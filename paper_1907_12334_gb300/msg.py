@@ -41,7 +41,8 @@ class msg_params(ctypes.Structure):
                 ("max_cycles", ctypes.c_int32), ("eps", ctypes.c_double), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("qoi", ctypes.c_int32), ("coef", ctypes.c_int32),
                 ("tune_block", ctypes.c_int32), ("tune_low_warps", ctypes.c_int32),
-                ("tune_low_items", ctypes.c_int32), ("tune_low_cut", ctypes.c_int32)]
+                ("tune_low_items", ctypes.c_int32), ("tune_low_cut", ctypes.c_int32),
+                ("tune_visit_smem", ctypes.c_int32)]
 
 
 @dataclass
@@ -60,11 +61,12 @@ class SolverParams:
     tune_low_warps: int = 0
     tune_low_items: int = 0
     tune_low_cut: int = 0    # schedule: highest diagonal inside the low-diagonal kernel (0 = default)
+    tune_visit_smem: int = 0  # schedule: KB of shared memory for shared-memory visits (0 = default, 1 = none)
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
                           self.qoi, self.coef, self.tune_block, self.tune_low_warps,
-                          self.tune_low_items, self.tune_low_cut)
+                          self.tune_low_items, self.tune_low_cut, self.tune_visit_smem)
 
 
 _lib = None

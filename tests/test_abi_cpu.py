@@ -74,7 +74,8 @@ def test_workspace_bytes_host_logic(lib):
                                     ([[3, 3]], {"eps": float("nan")}), ([[3, 3]], {"nu1": 65}),
                                     ([[3, 3]], {"tune_block": 48}), ([[3, 3]], {"tune_low_warps": 17}),
                                     ([[3, 3]], {"tune_low_items": 3}),
-                                    ([[3, 3]], {"tune_low_cut": 6}),
+                                    ([[3, 3]], {"tune_low_cut": 6}), ([[3, 3]], {"tune_visit_smem": 228}),
+                                    ([[3, 3]], {"tune_visit_smem": -1}),
                                     ([[3, 3]], {"tune_low_items": 8, "tune_low_warps": 8, "tune_low_cut": 5})])
 def test_invalid_arguments_rejected_on_host(lib, PQ, kw):
     assert _ws(PQ, **kw) == 0

@@ -217,6 +217,30 @@ def test_low_kernel_cut_changes_rounding_only(msg, cut, shape):
     np.testing.assert_allclose(got[0], Qo, rtol=1e-8)
 
 
+@pytest.mark.parametrize("limit", [1, 8, 227])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_shared_memory_visits_change_rounding_only(msg, limit, precision):
+    """Visits above the cut run on a shared-memory copy of their grid up to a
+    size limit and in global memory beyond it (1 KB: every visit in global
+    memory; 8 KB: the two paths on different diagonals of one hierarchy; 227 KB:
+    grids of up to 227 KB in shared memory).  The per-node arithmetic is the
+    same, so only the compiler's rounding of the cycles may differ: every grid
+    meets eps and the QoIs agree with the default limit and with the oracle."""
+    shapes = SHAPES_SMALL + [(2, 6), (6, 2), (5, 4), (6, 6), (8, 2), (1, 8)]
+    Zs = oracle_fields(shapes, seed=9)
+    kw = dict(eps=1e-10, max_cycles=300)
+    if precision == "fp64":
+        kw.update(precision=msg.MSG_PREC_FP64, eps=1e-11)
+    ref = run_gpu(msg, shapes, Zs, **kw)
+    got = run_gpu(msg, shapes, Zs, tune_visit_smem=limit, **kw)
+    assert (got[1] == 0).all() and (ref[1] == 0).all()
+    assert np.all(got[3] <= 1e-10)
+    tol = 1e-8 if precision == "mixed" else 1e-10
+    np.testing.assert_allclose(got[0], ref[0], rtol=tol)
+    Qo, _, _ = run_oracle(shapes, Zs, 1e-12, 600)
+    np.testing.assert_allclose(got[0], Qo, rtol=tol)
+
+
 # ------------------------------------------------------------------ (a14) --
 
 def test_mimc_differences_bit_exact(msg):
