@@ -263,7 +263,10 @@ def ours(a, rank, world, local_rank):
         msg.msg_normals(seed, 0, S, M, xi)
         msg.sample_field(prep, npts, M, gemm, xi, Z)
         prm = autotune.tune(PQ, Z.reshape(-1), prm, sample=min(S, 512))
-        tuned = {"tune_block": prm.tune_block, "tune_low_warps": prm.tune_low_warps}
+        tuned = {"tune_block": prm.tune_block, "tune_low_items": prm.tune_low_items,
+                 "tune_low_warps": prm.tune_low_warps}
+        del ws  # the tuned shapes may need another workspace size
+        ws = torch.empty(msg.msg_workspace_bytes(PQ, prm), dtype=torch.uint8, device=dev)
 
     def step(k):
         s0 = step_offset(k, world, rank, S)

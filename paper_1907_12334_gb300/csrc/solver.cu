@@ -549,7 +549,7 @@ __global__ void k_pre_res(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T
     const T* r = g.b;
     if (p > 1) {  // x-child (p-1, q): R_x around fine column 2ic, every interior row
         T* cxb = h.sbx + h.scr + grid_offset(p - 1, q, h.qi);
-        const int shc = p - 2, ncx = g.nx >> 1, Wc = ncx + 1, n = (g.ny - 1) << shc;
+        const int shc = p - 1, ncx = g.nx >> 1, Wc = ncx + 1, n = (g.ny - 1) << shc;  // ncx = 2^shc slots a row
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int ic = k & (ncx - 1), j = 1 + (k >> shc);
             if (ic == 0) continue;

@@ -1,6 +1,11 @@
-"""Host model of the streamed visit schedule (k_visit_stream in csrc/solver.cu).
+"""Host models of the shared-memory visit kernels (csrc/solver.cu).
 
-A grid too large for shared memory is swept through a ring of rows; in step t
+Resident visits (k_pre_res, k_post_res): the whole grid sits in shared memory
+with the columns split by parity; the model below replays their index
+arithmetic (colour-slot mapping, residual in place of b, restriction and
+prolongation slots) and must give, bit for bit, the phase-by-phase visit.
+
+Streamed visits (k_visit_stream): a grid too large for shared memory is swept through a ring of rows; in step t
 operation k of the visit's chain (PRE: 2 nu1 red-black colour phases, then the
 residual; POST: the prolongation, then 2 nu2 colour phases) works on row
 t - 2k, u row t - 2(2nu+1) is written back and PRE restricts the residual row
@@ -288,3 +293,109 @@ def test_a_ring_one_row_short_is_caught():
     with pytest.raises(AssertionError):
         stream_visit(False, u, b, ax, ay, nx, ny, nu, False, ucx=np.zeros((nx // 2 + 1) * (ny + 1)),
                      ring=AHEAD + 2 * (2 * nu + 1) + 1)
+
+
+# ------------------------------------------------------------- resident --
+
+def _colour_slots(p, ny, colour, h, W):
+    """(self, west) slots of the nodes of one colour, in the kernels' order."""
+    half, sh = (1 << p) >> 1, p - 1
+    for k in range((ny - 1) << sh):
+        j, kk = 1 + (k >> sh), k & (half - 1)
+        odd = (j + colour) & 1
+        if not odd and kk == half - 1:
+            continue
+        yield j * W + (h + kk if odd else kk + 1), j * W + (kk if odd else h + kk)
+
+
+def _res_load(u, b, ax, ay, p, q, zero):
+    nx, ny = 1 << p, 1 << q
+    W, h = nx + 1, nx // 2 + 1
+    S = {k: np.full(W * (ny + 1), np.nan) for k in "UBXY"}
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            c, s = j * W + i, j * W + split_slot(h, i)
+            S["U"][s], S["B"][s], S["X"][s], S["Y"][s] = 0.0 if zero else u[c], b[c], ax[c], ay[c]
+    return S, nx, ny, W, h
+
+
+def _res_smooth(S, p, ny, W, h, sweeps):
+    U, B, X, Y = S["U"], S["B"], S["X"], S["Y"]
+    for _ in range(sweeps):
+        for colour in (0, 1):
+            for s, w in list(_colour_slots(p, ny, colour, h, W)):
+                aw, ae, as_, an = X[w], X[s], Y[s - W], Y[s]
+                nb = (aw * U[w] + ae * U[w + 1]) + (as_ * U[s - W] + an * U[s + W])
+                U[s] = (B[s] + nb) * (1.0 / (aw + ae + as_ + an))
+
+
+def _res_store(S, nx, ny, W, h):
+    return np.array([S["U"][j * W + split_slot(h, i)] for j in range(ny + 1) for i in range(nx + 1)])
+
+
+def resident_pre(u, b, ax, ay, p, q, nu, zero):
+    S, nx, ny, W, h = _res_load(u, b, ax, ay, p, q, zero)
+    _res_smooth(S, p, ny, W, h, nu)
+    U, B, X, Y = S["U"], S["B"], S["X"], S["Y"]
+    for colour in (0, 1):
+        for s, w in list(_colour_slots(p, ny, colour, h, W)):
+            aw, ae, as_, an = X[w], X[s], Y[s - W], Y[s]
+            B[s] = B[s] - ((aw + ae + as_ + an) * U[s] - (aw * U[w] + ae * U[w + 1]) - (as_ * U[s - W] + an * U[s + W]))
+    cxb, cyb = {}, {}
+    if p > 1:  # k = (row, ic) with ncx = 2^(p-1) slots a row
+        shc, ncx = p - 1, nx >> 1
+        for k in range((ny - 1) << shc):
+            ic, j = k & (ncx - 1), 1 + (k >> shc)
+            if ic:
+                base = j * W
+                cxb[j * (ncx + 1) + ic] = 0.25 * (B[base + h + ic - 1] + 2.0 * B[base + ic] + B[base + h + ic])
+    if q > 1:
+        for k in range(((ny >> 1) - 1) << p):
+            i, jc = k & (nx - 1), 1 + (k >> p)
+            if i:
+                s = 2 * jc * W + split_slot(h, i)
+                cyb[jc * W + i] = 0.25 * (B[s - W] + 2.0 * B[s] + B[s + W])
+    return _res_store(S, nx, ny, W, h), cxb, cyb
+
+
+def resident_post(u, b, ax, ay, p, q, nu, ucx, ucy, omega):
+    S, nx, ny, W, h = _res_load(u, b, ax, ay, p, q, False)
+    U, X, Y = S["U"], S["X"], S["Y"]
+    for k in range((ny - 1) << p):
+        i, j = k & (nx - 1), 1 + (k >> p)
+        if i == 0:
+            continue
+        s, w = j * W + split_slot(h, i), j * W + split_slot(h, i - 1)
+        U[s] += omega * prolong_corr(None, None, None, W, i, j, nx, ucx, ucy, X[w], X[s], Y[s - W], Y[s])
+    _res_smooth(S, p, ny, W, h, nu)
+    return _res_store(S, nx, ny, W, h)
+
+
+RES_CASES = [(1, 3, 2), (2, 2, 2), (3, 4, 2), (2, 5, 2), (4, 3, 2), (5, 2, 2), (3, 3, 1), (4, 4, 0), (2, 1, 2),
+             (1, 1, 2)]
+
+
+@pytest.mark.parametrize("p,q,nu", RES_CASES)
+def test_resident_pre_equals_phase_order(p, q, nu):
+    """Every child right-hand-side entry is written (same key sets) with the
+    phase-order value; a wrong row/slot shift in the restriction fails here."""
+    nx, ny = 1 << p, 1 << q
+    u, b, ax, ay, _ = _grid(nx, ny, 5 * p + q)
+    for zero in (False, True):
+        ru, rcx, rcy = ref_pre(u, b, ax, ay, nx, ny, nu, zero)
+        gu, gcx, gcy = resident_pre(u, b, ax, ay, p, q, nu, zero)
+        assert np.array_equal(gu, ru)
+        assert gcx == rcx and gcy == rcy
+
+
+@pytest.mark.parametrize("p,q,nu", RES_CASES)
+def test_resident_post_equals_phase_order(p, q, nu):
+    nx, ny = 1 << p, 1 << q
+    u, b, ax, ay, rng = _grid(nx, ny, 13 * p + q)
+    for has_x, has_y in itertools.product((False, True), repeat=2):
+        if (has_x and p == 1) or (has_y and q == 1) or not (has_x or has_y):
+            continue
+        ucx = rng.standard_normal((nx // 2 + 1) * (ny + 1)) if has_x else None
+        ucy = rng.standard_normal((nx + 1) * (ny // 2 + 1)) if has_y else None
+        assert np.array_equal(resident_post(u, b, ax, ay, p, q, nu, ucx, ucy, 0.9),
+                              ref_post(u, b, ax, ay, nx, ny, nu, ucx, ucy, 0.9))
