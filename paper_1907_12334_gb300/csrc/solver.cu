@@ -415,26 +415,25 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
     visit_post(CtaGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
-// ------------------------------------------- shared-memory resident visits --
+// --------------------------------------------- register-cached visits --
 //
-// A visit whose grid fits in shared memory reads u, b and the coefficients
-// once, runs the sweeps, the residual and the restriction (PRE) or the
-// prolongation and the sweeps (POST) on that copy, and writes u and the
-// children's right-hand sides once: one trip to L2/DRAM per visit instead of
-// one per colour phase.  Each shared plane keeps the grid's rows (stride
-// W = nx + 1) with the columns split by parity, even i in slots 0..nx/2 and
-// odd i in the slots after them, so that the nodes of one colour in a row and
+// Full launches of the global-memory visits above are bound by instruction
+// issue, not by memory: the grid is served from L1 after its first touch, and
+// every colour phase repeats the node's index arithmetic and reloads its four
+// face coefficients and its right-hand side.  None of those change during a
+// visit.  Here a thread keeps, for each of its nodes, the four coefficients,
+// their sum and its reciprocal, and b in registers for the whole visit, and u
+// sits in shared memory; a sweep then costs a node four shared loads, two
+// fused multiply-adds, a multiply and a store.  Thread t owns colour slot
+// t + m blockDim (m < NPT) of each colour.  The shared plane keeps the grid's
+// rows (stride W = nx + 1) with the columns split by parity, even i in slots
+// 0..nx/2 and odd i after them, so that the nodes of one colour in a row and
 // each of their neighbours sit at consecutive addresses.  The arithmetic of a
-// node is that of the global-memory visits above (same expressions).
+// node is written with explicit fma, so every launch shape (threads, NPT)
+// rounds alike.  Grids with more than 512 NPT nodes of a colour keep the
+// global-memory visits.
 
-template <class T>
-struct SGrid {
-    T* u;   // shared planes, (ny + 1) rows of W slots
-    T* b;   // right-hand side; the residual replaces it in PRE
-    T* ax;
-    T* ay;
-    int p, nx, ny, W, h;  // h = nx/2 + 1: slot of column 1
-};
+constexpr int kRegThreadsMax = 512;  // threads per CTA of the register-cached visits
 
 __device__ __forceinline__ int split_slot(int h, int i) { return (i & 1) ? h + (i >> 1) : (i >> 1); }
 
@@ -458,266 +457,90 @@ __device__ __forceinline__ void for_each_node(int p, int ny, F f)
     }
 }
 
-// Calls f(self, west) for every node of colour `colour` (0: red, (i+j) even)
-// with self and west the row-relative slots of the node and of its west
-// neighbour (the east one is west + 1); base = j W is added by f's caller.
-template <class T, class F>
-__device__ __forceinline__ void for_each_colour(const SGrid<T>& g, int colour, F f)
+// Node of colour slot k (colour 0: red, (i+j) even): k = (j-1) nx/2 + kk with
+// i = 2kk + 1 when i has the parity (j + colour) & 1 == 1, else i = 2kk + 2
+// (kk = nx/2 - 1 is then the boundary and no node).  Returns false for no node.
+__device__ __forceinline__ bool colour_node(int k, int colour, int p, int& i, int& j)
 {
-    const int sh = g.p - 1, half = g.nx >> 1, n = (g.ny - 1) << sh;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int j = 1 + (k >> sh), kk = k & (half - 1);
-        const int odd = (j + colour) & 1;  // parity of i: i = 2kk + 1 (odd) or 2kk + 2 (even)
-        if (!odd && kk == half - 1) continue;
-        const int base = j * g.W;
-        f(base + (odd ? g.h + kk : kk + 1), base + (odd ? kk : g.h + kk));
-    }
+    const int sh = p - 1, half = 1 << sh;
+    j = 1 + (k >> sh);
+    const int kk = k & (half - 1), odd = (j + colour) & 1;
+    i = odd ? 2 * kk + 1 : 2 * kk + 2;
+    return odd || kk != half - 1;
 }
 
-template <class T>
-__device__ __forceinline__ void res_smooth(const SGrid<T>& g, int sweeps)
-{
-    const int W = g.W;
-    for (int sw = 0; sw < sweeps; ++sw)
-        for (int colour = 0; colour < 2; ++colour) {
-            for_each_colour(g, colour, [&](int s, int w) {
-                T aw = g.ax[w], ae = g.ax[s], as = g.ay[s - W], an = g.ay[s];
-                T nb = (aw * g.u[w] + ae * g.u[w + 1]) + (as * g.u[s - W] + an * g.u[s + W]);
-                g.u[s] = (g.b[s] + nb) * rcp_of(aw + ae + as + an);
-            });
-            __syncthreads();
-        }
-}
+// Rounding pinned: no contraction into or out of these.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// Stages the visited grid: u (or zeros), b and the coefficients.
-template <class T>
-__device__ __forceinline__ SGrid<T> res_load(T* smem, const GView<T>& gv, int p, int q, bool zero_u)
+// One visit half: PRE (pre = 1) = (zero,) nu red-black sweeps, residual and
+// Eq. (2.3) restriction into the children's right-hand sides; POST = the
+// Eq. (2.4)/(2.5) coarse-grid correction, then nu sweeps.  One CTA per (item,
+// grid), NPT nodes of each colour per thread.
+template <class T, int NPT>
+__global__ void __launch_bounds__(kRegThreadsMax) k_visit_reg(DevCtx cx, T* su, T* sbx, T* sby, const T* ax,
+                                                              const T* ay, int pre, int zero_init, int nu,
+                                                              double omega_d)
 {
-    SGrid<T> g;
-    g.p = p;
-    g.nx = 1 << p;
-    g.ny = 1 << q;
-    g.W = g.nx + 1;
-    g.h = (g.nx >> 1) + 1;
-    const int n = g.W * (g.ny + 1);
-    g.u = smem;
-    g.b = smem + n;
-    g.ax = smem + 2 * n;
-    g.ay = smem + 3 * n;
-    for_each_node(p, g.ny, [&](int j, int i) {
-        const int c = j * g.W + i, s = j * g.W + split_slot(g.h, i);
-        if (zero_u) g.u[s] = T(0);
-        else cp_async_elem(g.u + s, gv.u + c);
-        cp_async_elem(g.ax + s, gv.ax + c);
-        cp_async_elem(g.ay + s, gv.ay + c);
-        if (gv.bmode == 0) cp_async_elem(g.b + s, gv.bx + c);
-        else if (gv.bmode == 1) cp_async_elem(g.b + s, gv.by + c);
-        else g.b[s] = b_at(gv, c);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
+    const Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    const int p = t.seg->p, q = t.seg->q;
+    const GView<T> gv = view_of(h, p, q);
+    const int nx = 1 << p, ny = 1 << q, W = nx + 1, hs = (nx >> 1) + 1, nslot = (ny - 1) << (p - 1);
+    T* U = (T*)smem_raw;
+    T* Rs = U + W * (ny + 1);  // PRE: the residual
+    const bool zu = pre && zero_init;
+    for_each_node(p, ny, [&](int j, int i) {
+        T* d = U + j * W + split_slot(hs, i);
+        if (zu) *d = T(0);
+        else cp_async_elem(d, gv.u + j * W + i);
     });
+    // the thread's nodes: slots, coefficients, diagonal, its reciprocal, b
+    T aw[2][NPT], ae[2][NPT], as[2][NPT], an[2][NPT], dg[2][NPT], iv[2][NPT], bb[2][NPT];
+    int ss[2][NPT], ww[2][NPT];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < NPT; ++m) {
+            const int k = threadIdx.x + m * blockDim.x;
+            int i = 0, j = 0;
+            ss[c][m] = -1;
+            ww[c][m] = 0;
+            aw[c][m] = ae[c][m] = as[c][m] = an[c][m] = dg[c][m] = iv[c][m] = bb[c][m] = T(0);
+            if (k < nslot && colour_node(k, c, p, i, j)) {
+                const int g = j * W + i;
+                ss[c][m] = j * W + split_slot(hs, i);
+                ww[c][m] = j * W + split_slot(hs, i - 1);
+                aw[c][m] = gv.ax[g - 1];
+                ae[c][m] = gv.ax[g];
+                as[c][m] = gv.ay[g - W];
+                an[c][m] = gv.ay[g];
+                dg[c][m] = aw[c][m] + ae[c][m] + as[c][m] + an[c][m];
+                iv[c][m] = rcp_of(dg[c][m]);
+                bb[c][m] = b_at(gv, g);
+            }
+        }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    return g;
-}
-
-template <class T>
-__device__ __forceinline__ void res_store_u(const SGrid<T>& g, T* u)
-{
-    for_each_node(g.p, g.ny, [&](int j, int i) { u[j * g.W + i] = g.u[j * g.W + split_slot(g.h, i)]; });
-}
-
-// PRE half of a visit in shared memory: (zero,) nu1 sweeps, residual, Eq. (2.3).
-template <class T>
-__global__ void k_pre_res(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int zero_init, int nu1)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TaskRef t;
-    if (!resolve_2d(cx, t)) return;
-    const Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    const int p = t.seg->p, q = t.seg->q;
-    const GView<T> gv = view_of(h, p, q);
-    const SGrid<T> g = res_load((T*)smem_raw, gv, p, q, zero_init != 0);
-    res_smooth(g, nu1);
-    const int W = g.W;
-    for (int colour = 0; colour < 2; ++colour)  // r = b - A u into b (each node reads only its own b)
-        for_each_colour(g, colour, [&](int s, int w) {
-            T aw = g.ax[w], ae = g.ax[s], as = g.ay[s - W], an = g.ay[s];
-            T Au = (aw + ae + as + an) * g.u[s] - (aw * g.u[w] + ae * g.u[w + 1]) - (as * g.u[s - W] + an * g.u[s + W]);
-            g.b[s] = g.b[s] - Au;
-        });
-    __syncthreads();
-    res_store_u(g, gv.u);
-    const T* r = g.b;
-    if (p > 1) {  // x-child (p-1, q): R_x around fine column 2ic, every interior row
-        T* cxb = h.sbx + h.scr + grid_offset(p - 1, q, h.qi);
-        const int shc = p - 1, ncx = g.nx >> 1, Wc = ncx + 1, n = (g.ny - 1) << shc;  // ncx = 2^shc slots a row
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int ic = k & (ncx - 1), j = 1 + (k >> shc);
-            if (ic == 0) continue;
-            const int base = j * W;  // fine columns 2ic-1, 2ic, 2ic+1: slots h+ic-1, ic, h+ic
-            cxb[j * Wc + ic] = T(0.25) * (r[base + g.h + ic - 1] + T(2) * r[base + ic] + r[base + g.h + ic]);
-        }
-    }
-    if (q > 1) {  // y-child (p, q-1): R_y around fine row 2jc, every interior column
-        T* cyb = h.sby + h.scr + grid_offset(p, q - 1, h.qi);
-        const int n = ((g.ny >> 1) - 1) << p;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int i = k & (g.nx - 1), jc = 1 + (k >> p);
-            if (i == 0) continue;
-            const int s = 2 * jc * W + split_slot(g.h, i);
-            cyb[jc * W + i] = T(0.25) * (r[s - W] + T(2) * r[s] + r[s + W]);
-        }
-    }
-}
-
-// POST half in shared memory: Eq. (2.4)/(2.5) correction, nu2 sweeps.
-template <class T>
-__global__ void k_post_res(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int nu2, double omega_d)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TaskRef t;
-    if (!resolve_2d(cx, t)) return;
-    const Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    const int p = t.seg->p, q = t.seg->q;
-    const GView<T> gv = view_of(h, p, q);
-    const SGrid<T> g = res_load((T*)smem_raw, gv, p, q, false);
-    const T omega = (T)omega_d;
-    const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
-    const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    const int W = g.W, n = (g.ny - 1) << p;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int i = k & (g.nx - 1), j = 1 + (k >> p);
-        if (i == 0) continue;
-        const int s = j * W + split_slot(g.h, i), w = j * W + split_slot(g.h, i - 1);
-        T vx = T(0), vy = T(0);
-        if (ucx) {
-            const int Wc = (g.nx >> 1) + 1, r = j * Wc + (i >> 1);
-            vx = (i & 1) ? T(0.5) * (ucx[r] + ucx[r + 1]) : ucx[r];
-        }
-        if (ucy) {
-            const int r = (j >> 1) * W + i;
-            vy = (j & 1) ? T(0.5) * (ucy[r] + ucy[r + W]) : ucy[r];
-        }
-        T corr;
-        if (ucx && ucy) {
-            T cxv = g.ax[w] + g.ax[s], cyv = g.ay[s - W] + g.ay[s];
-            T x2 = cxv * cxv, y2 = cyv * cyv, sc = rcp_of(x2 + y2);
-            corr = (x2 * sc) * vx + (y2 * sc) * vy;
-        } else {
-            corr = ucx ? vx : vy;
-        }
-        g.u[s] += omega * corr;
-    }
-    __syncthreads();
-    res_smooth(g, nu2);
-    res_store_u(g, gv.u);
-}
-
-// ------------------------------------------------ streamed visits (rows) --
-//
-// A grid too large for shared memory is swept row by row through a ring of
-// rows of u, b, ax and ay (the same split-column layout), filled kStreamAhead
-// rows ahead of use by cp.async.  A visit is a chain of 2 nu + 1 operations
-// on rows: PRE = 2 nu1 colour phases, then the residual (into b); POST = the
-// prolongation, then 2 nu2 colour phases.  In step t operation k works on row
-// t - 2k.  An operation on row j reads rows j-1..j+1 as the previous operation
-// left them: that operation finished row j+1 in an earlier step, and no other
-// operation of step t touches rows j-1..j+1 in the planes it reads (the rows of
-// operations k-1 and k+1 are two rows away).  Red-black Gauss-Seidel, the
-// residual and the prolongation therefore give the values of the phase-by-phase
-// order.  Behind the chain, row t - 2(2 nu + 1) of u goes back to global memory,
-// and PRE restricts the residual rows the chain has finished (Eq. (2.3)).  The
-// ring holds R = kStreamAhead + 2 (2 nu + 1) + 3 rows: the row a step loads was
-// last read three rows behind the write-back of the step before.
-
-constexpr int kStreamAhead = 4;
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <class T>
-__global__ void k_visit_stream(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, int pre, int zero_init,
-                               int nu, double omega_d, int R)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TaskRef t;
-    if (!resolve_2d(cx, t)) return;
-    const Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
-    const int p = t.seg->p, q = t.seg->q;
-    const GView<T> gv = view_of(h, p, q);
-    const int nx = 1 << p, ny = 1 << q, W = nx + 1, hs = (nx >> 1) + 1, half = nx >> 1;
-    const int Rr = min(R, ny + 1);  // a ring of ny + 1 rows holds the whole grid
-    T* U = (T*)smem_raw;
-    T* B = U + Rr * W;
-    T* AX = B + Rr * W;
-    T* AY = AX + Rr * W;
-    const bool zu = pre && zero_init;
-    const int nops = 2 * nu + 1, ncol = 2 * nu * half;
-    const T omega = (T)omega_d;
-    const T* ucx = (!pre && p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
-    const T* ucy = (!pre && q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    T* cxb = (pre && p > 1) ? h.sbx + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
-    T* cyb = (pre && q > 1) ? h.sby + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
-    auto rowb = [&](int j) { return (j % Rr) * W; };
-    auto load_row = [&](int j) {
-        const int rb = rowb(j);
-        for (int i = threadIdx.x; i <= nx; i += blockDim.x) {
-            const int c = j * W + i, s = rb + split_slot(hs, i);
-            if (zu) U[s] = T(0);
-            else cp_async_elem(U + s, gv.u + c);
-            cp_async_elem(AX + s, gv.ax + c);
-            cp_async_elem(AY + s, gv.ay + c);
-            if (gv.bmode == 0) cp_async_elem(B + s, gv.bx + c);
-            else if (gv.bmode == 1) cp_async_elem(B + s, gv.by + c);
-            else B[s] = b_at(gv, c);
-        }
-    };
-    for (int j = 0; j < kStreamAhead; ++j) {
-        if (j <= ny) load_row(j);
-        cp_async_commit();
-    }
-    const int steps = ny + 2 * nops + 1;  // the last write-back is row ny
-    for (int st = 0; st < steps; ++st) {
-        if (st + kStreamAhead <= ny) load_row(st + kStreamAhead);
-        cp_async_commit();
-        asm volatile("cp.async.wait_group %0;" ::"n"(kStreamAhead - 1) : "memory");  // rows <= st + 1 are in
-        __syncthreads();
-        // the chain: colour phases use nx/2 slots of a row, the residual and the
-        // prolongation nx slots
-        for (int w = threadIdx.x; w < ncol + nx; w += blockDim.x) {
-            int k, m;
-            if (pre) {
-                if (w < ncol) { k = w >> (p - 1); m = w & (half - 1); }
-                else { k = 2 * nu; m = w - ncol; }
-            } else {
-                if (w < nx) { k = 0; m = w; }
-                else { k = 1 + ((w - nx) >> (p - 1)); m = (w - nx) & (half - 1); }
-            }
-            const int j = st - 2 * k;
-            if (j < 1 || j > ny - 1) continue;
-            const int b0 = rowb(j), bm = rowb(j - 1), bp = rowb(j + 1);
-            if (pre ? (k < 2 * nu) : (k > 0)) {  // colour phase
-                const int colour = pre ? (k & 1) : ((k - 1) & 1);
-                const int odd = (j + colour) & 1;
-                if (!odd && m == half - 1) continue;
-                const int s = odd ? hs + m : m + 1, wv = odd ? m : hs + m;
-                T aw = AX[b0 + wv], ae = AX[b0 + s], as = AY[bm + s], an = AY[b0 + s];
-                T nb = (aw * U[b0 + wv] + ae * U[b0 + wv + 1]) + (as * U[bm + s] + an * U[bp + s]);
-                U[b0 + s] = (B[b0 + s] + nb) * rcp_of(aw + ae + as + an);
-            } else if (pre) {  // residual into b, slots of both colours
-                const int colour = m >= half, kk = m - colour * half;
-                const int odd = (j + colour) & 1;
-                if (!odd && kk == half - 1) continue;
-                const int s = odd ? hs + kk : kk + 1, wv = odd ? kk : hs + kk;
-                T aw = AX[b0 + wv], ae = AX[b0 + s], as = AY[bm + s], an = AY[b0 + s];
-                T Au = (aw + ae + as + an) * U[b0 + s] - (aw * U[b0 + wv] + ae * U[b0 + wv + 1]) -
-                       (as * U[bm + s] + an * U[bp + s]);
-                B[b0 + s] = B[b0 + s] - Au;
-            } else {  // prolongation, Eq. (2.4)/(2.5), at column i = m
-                const int i = m;
-                if (i == 0) continue;
-                const int s = b0 + split_slot(hs, i), wv = b0 + split_slot(hs, i - 1);
+    if (!pre) {  // coarse-grid correction from the children's corrections (global memory)
+        const T omega = (T)omega_d;
+        const T* ucx = (p > 1) ? h.su + h.scr + grid_offset(p - 1, q, h.qi) : nullptr;
+        const T* ucy = (q > 1) ? h.su + h.scr + grid_offset(p, q - 1, h.qi) : nullptr;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                int i, j;
+                const int s = ss[c][m];
+                if (s < 0) continue;
+                colour_node(threadIdx.x + m * blockDim.x, c, p, i, j);
                 T vx = T(0), vy = T(0);
                 if (ucx) {
-                    const int Wc = half + 1, r = j * Wc + (i >> 1);
+                    const int r = j * (hs) + (i >> 1);  // child row stride nx/2 + 1 = hs
                     vx = (i & 1) ? T(0.5) * (ucx[r] + ucx[r + 1]) : ucx[r];
                 }
                 if (ucy) {
@@ -726,37 +549,66 @@ __global__ void k_visit_stream(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, co
                 }
                 T corr;
                 if (ucx && ucy) {
-                    T cxv = AX[wv] + AX[s], cyv = AY[bm + (s - b0)] + AY[s];
-                    T x2 = cxv * cxv, y2 = cyv * cyv, sc = rcp_of(x2 + y2);
-                    corr = (x2 * sc) * vx + (y2 * sc) * vy;
+                    const T cxv = aw[c][m] + ae[c][m], cyv = as[c][m] + an[c][m];
+                    const T x2 = mul_rn(cxv, cxv), y2 = mul_rn(cyv, cyv), sc = rcp_of(x2 + y2);
+                    corr = fma_rn(mul_rn(x2, sc), vx, mul_rn(mul_rn(y2, sc), vy));
                 } else {
                     corr = ucx ? vx : vy;
                 }
-                U[s] += omega * corr;
+                U[s] = fma_rn(omega, corr, U[s]);
             }
-        }
-        // behind the chain: rows no operation of this step writes
-        const int jw = st - 2 * nops;
-        if (jw >= 0 && jw <= ny) {
-            const int rb = rowb(jw);
-            for (int i = threadIdx.x; i <= nx; i += blockDim.x) gv.u[jw * W + i] = U[rb + split_slot(hs, i)];
-        }
-        const int jr = jw + 1;  // residual row finished in the previous step
-        if (cxb && jr >= 1 && jr <= ny - 1) {
-            const int rb = rowb(jr), ncx = half, Wc = ncx + 1;
-            for (int ic = 1 + threadIdx.x; ic < ncx; ic += blockDim.x)
-                cxb[jr * Wc + ic] = T(0.25) * (B[rb + hs + ic - 1] + T(2) * B[rb + ic] + B[rb + hs + ic]);
-        }
-        if (cyb && (jr & 1) && jr >= 3 && jr <= ny - 1) {
-            const int jc = (jr - 1) >> 1, r0 = rowb(jr - 2), r1 = rowb(jr - 1), r2 = rowb(jr);
-            for (int i = 1 + threadIdx.x; i < nx; i += blockDim.x) {
-                const int s = split_slot(hs, i);
-                cyb[jc * W + i] = T(0.25) * (B[r0 + s] + T(2) * B[r1 + s] + B[r2 + s]);
+        __syncthreads();
+    }
+    for (int sw = 0; sw < nu; ++sw)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                const int s = ss[c][m], w = ww[c][m];
+                if (s < 0) continue;
+                const T nb = fma_rn(aw[c][m], U[w], mul_rn(ae[c][m], U[w + 1])) +
+                             fma_rn(as[c][m], U[s - W], mul_rn(an[c][m], U[s + W]));
+                U[s] = (bb[c][m] + nb) * iv[c][m];
             }
+            __syncthreads();
+        }
+    if (pre) {  // r = b - A u at every interior node
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                const int s = ss[c][m], w = ww[c][m];
+                if (s < 0) continue;
+                const T xw = fma_rn(aw[c][m], U[w], mul_rn(ae[c][m], U[w + 1]));
+                const T xs = fma_rn(as[c][m], U[s - W], mul_rn(an[c][m], U[s + W]));
+                Rs[s] = bb[c][m] - (fma_rn(dg[c][m], U[s], -xw) - xs);
+            }
+        __syncthreads();
+    }
+    for_each_node(p, ny, [&](int j, int i) { gv.u[j * W + i] = U[j * W + split_slot(hs, i)]; });
+    if (!pre) return;
+    if (p > 1) {  // x-child (p-1, q): R_x around fine column 2ic of every interior row
+        T* cxb = h.sbx + h.scr + grid_offset(p - 1, q, h.qi);
+        const int shc = p - 1, ncx = nx >> 1, Wc = ncx + 1, n = (ny - 1) << shc;  // ncx = 2^shc slots a row
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int ic = k & (ncx - 1), j = 1 + (k >> shc);
+            if (ic == 0) continue;
+            const int base = j * W;  // fine columns 2ic-1, 2ic, 2ic+1: slots hs+ic-1, ic, hs+ic
+            cxb[j * Wc + ic] = T(0.25) * (Rs[base + hs + ic - 1] + T(2) * Rs[base + ic] + Rs[base + hs + ic]);
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (q > 1) {  // y-child (p, q-1): R_y around fine row 2jc of every interior column
+        T* cyb = h.sby + h.scr + grid_offset(p, q - 1, h.qi);
+        const int n = ((ny >> 1) - 1) << p;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int i = k & (nx - 1), jc = 1 + (k >> p);
+            if (i == 0) continue;
+            const int s = 2 * jc * W + split_slot(hs, i);
+            cyb[jc * W + i] = T(0.25) * (Rs[s - W] + T(2) * Rs[s] + Rs[s + W]);
+        }
+    }
 }
+
 
 // ---------------------------------------------- table-driven low diagonals --
 //
@@ -2422,21 +2274,27 @@ static int stage_worker(const SolveCtx<T>& C, int L, StageQueues& Qs, cudaStream
             // threads per CTA: every grid of diagonal d has 2^(d+2) cells, 2^(d+1) points per
             // colour; small grids get no idle warps, the big ones (d >= 10) twice the block
             const int vb = d >= 10 ? std::min(2 * C.block, 1024) : std::min(C.block, std::max(32, 1 << (d + 1)));
-            // the whole grid in shared memory when its four planes fit the limit, else a
-            // ring of rows when that fits a CTA, else the visit in global memory
-            const int nu = pre ? C.prm.nu1 : C.prm.nu2, R = kStreamAhead + 2 * (2 * nu + 1) + 3;
-            int64_t nodes = 0, ring = 0;
+            // register-cached visit when every grid of the launch has at most
+            // kRegThreadsMax x NPT nodes of a colour and its shared planes (u; PRE also r)
+            // fit the limit; else the global-memory visit
+            const int nu = pre ? C.prm.nu1 : C.prm.nu2;
+            int64_t nodes = 0, nslot = 0;
             for (size_t k = dseg0[d]; k < dseg0[d] + dnseg[d]; ++k) {
-                const int64_t W = (1 << h_segs[k].p) + 1, H = (1 << h_segs[k].q) + 1;
-                nodes = std::max<int64_t>(nodes, W * H);
-                ring = std::max<int64_t>(ring, W * std::min<int64_t>(R, H));
+                const int sp = h_segs[k].p, sq = h_segs[k].q;
+                nodes = std::max<int64_t>(nodes, (int64_t)((1 << sp) + 1) * ((1 << sq) + 1));
+                nslot = std::max<int64_t>(nslot, (int64_t)((1 << sq) - 1) << (sp - 1));
             }
-            const size_t rsm = 4 * (size_t)nodes * sizeof(T), ssm = 4 * (size_t)ring * sizeof(T);
-            if (rsm <= C.visit_smem) {
-                if (pre) k_pre_res<T><<<g2, vb, rsm, st>>>(c, su, sbx, sby, C.ax, C.ay, zi, C.prm.nu1);
-                else k_post_res<T><<<g2, vb, rsm, st>>>(c, su, sbx, sby, C.ax, C.ay, C.prm.nu2, C.prm.omega);
-            } else if (C.visit_smem > 1024 && ssm <= kSmemMax) {
-                k_visit_stream<T><<<g2, vb, ssm, st>>>(c, su, sbx, sby, C.ax, C.ay, pre, zi, nu, C.prm.omega, R);
+            const int nptmax = sizeof(T) == 4 ? 4 : 2;  // FP64 nodes take twice the registers
+            int npt = 1;
+            while (npt < nptmax && (nslot + npt - 1) / npt > C.block) npt *= 2;
+            const int vr = (int)std::max<int64_t>(32, ((nslot + npt - 1) / npt + 31) / 32 * 32);
+            const size_t rsm = (pre ? 2 : 1) * (size_t)nodes * sizeof(T);
+            if (vr <= kRegThreadsMax && rsm <= C.visit_smem) {
+                const double om = C.prm.omega;
+                if (npt == 1) k_visit_reg<T, 1><<<g2, vr, rsm, st>>>(c, su, sbx, sby, C.ax, C.ay, pre, zi, nu, om);
+                else if (npt == 2) k_visit_reg<T, 2><<<g2, vr, rsm, st>>>(c, su, sbx, sby, C.ax, C.ay, pre, zi, nu, om);
+                else if constexpr (sizeof(T) == 4)
+                    k_visit_reg<T, 4><<<g2, vr, rsm, st>>>(c, su, sbx, sby, C.ax, C.ay, pre, zi, nu, om);
             } else if (pre) {
                 // residual band of the restriction: the whole grid when it has at most
                 // kBandNodes nodes, else bands of at least 3 rows
@@ -2560,9 +2418,11 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     // the residual band: 3 rows of a 2^12-cell-wide grid at most
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(T) * std::max(kBandNodes, 3 * ((1 << 12) + 1)))));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_pre_res<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_post_res<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    MSG_CUDA_TRY(cudaFuncSetAttribute(k_visit_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_visit_reg<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    MSG_CUDA_TRY(cudaFuncSetAttribute(k_visit_reg<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    if constexpr (sizeof(T) == 4)
+        MSG_CUDA_TRY(cudaFuncSetAttribute(k_visit_reg<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSmemMax));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     MSG_CUDA_TRY(cudaFuncSetAttribute(k_lowv<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));

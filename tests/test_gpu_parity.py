@@ -220,12 +220,13 @@ def test_low_kernel_cut_changes_rounding_only(msg, cut, shape):
 @pytest.mark.parametrize("limit", [1, 8, 227])
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_shared_memory_visits_change_rounding_only(msg, limit, precision):
-    """Visits above the cut run on a shared-memory copy of their grid up to a
-    size limit and in global memory beyond it (1 KB: every visit in global
-    memory; 8 KB: the two paths on different diagonals of one hierarchy; 227 KB:
-    grids of up to 227 KB in shared memory).  The per-node arithmetic is the
-    same, so only the compiler's rounding of the cycles may differ: every grid
-    meets eps and the QoIs agree with the default limit and with the oracle."""
+    """Visits above the cut run register-cached (u in shared memory, each
+    node's coefficients and right-hand side in registers) up to a shared-memory
+    limit and in global memory beyond it (1 KB: every visit in global memory;
+    8 KB: the two paths on different diagonals of one hierarchy; 227 KB: every
+    grid small enough for the register path).  The per-node arithmetic is the
+    same up to the compiler's rounding: every grid meets eps and the QoIs agree
+    with the default limit and with the oracle."""
     shapes = SHAPES_SMALL + [(2, 6), (6, 2), (5, 4), (6, 6), (8, 2), (1, 8)]
     Zs = oracle_fields(shapes, seed=9)
     kw = dict(eps=1e-10, max_cycles=300)
