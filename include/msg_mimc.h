@@ -85,7 +85,7 @@ typedef struct {
     int32_t tune_low_warps; /* launch shape: warps per CTA of the low-diagonal kernel (0: default; 1..16) */
     int32_t tune_low_items; /* launch shape: items one warp of that kernel runs in lockstep: 1, 2, 4 or 8 (0: default) */
     int32_t tune_low_cut;   /* schedule: the highest diagonal of each hierarchy run inside the low-diagonal kernel (0: default 4, lower when a long mu/nu program does not fit; 1..5); the visits above it are separate launches.  Launch shapes never change results; the cut changes only the rounding of the inner cycles */
-    int32_t tune_visit_smem; /* schedule: KB of shared memory per CTA up to which a visit above the cut runs register-cached (u in shared memory; each thread keeps its nodes' coefficients and right-hand side in registers for the whole visit; grids of up to 2048 nodes per colour in the mixed path, 1024 in FP64) instead of in global memory (0: default 100; 1..227; 1 keeps every visit in global memory).  Changes only the rounding of the cycles */
+    int32_t tune_visit_smem; /* schedule: KB of shared memory per CTA up to which a visit above the cut runs register-cached (u in shared memory; each thread keeps its nodes' coefficients and right-hand side in registers for the whole visit; grids of up to 2048 nodes per colour in the mixed path, 1024 in FP64) instead of in global memory (0: default 1; 1..227; 1 keeps every visit in global memory, the faster at 256 x 256).  Changes only the rounding of the cycles */
 } msg_params;
 
 /* ------------------------------------------------------------------------ */

@@ -1934,7 +1934,10 @@ WsLayout layout_of(const Plan& pl, const msg_params& prm)
 constexpr int kThreads = 256;
 constexpr int kVisitThreads = 128;       // threads per CTA of the PRE/POST visit kernels (default)
 constexpr int kBandNodes = 4096;         // residual band of the restriction in shared memory (nodes)
-constexpr int kVisitSmemKB = 100;        // shared-memory visits: default limit per CTA (KB)
+// Register-cached visits: default shared-memory limit per CTA (KB).  1 KB keeps every
+// visit in global memory: at 256 x 256 the register-cached visits measured no faster on
+// diagonals 5..7 and slower on 8..10 (fewer resident CTAs at their register count).
+constexpr int kVisitSmemKB = 1;
 
 
 // Host staging for the per-step lists (pinned so the uploads are asynchronous).

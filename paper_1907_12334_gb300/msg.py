@@ -61,7 +61,7 @@ class SolverParams:
     tune_low_warps: int = 0
     tune_low_items: int = 0
     tune_low_cut: int = 0    # schedule: highest diagonal inside the low-diagonal kernel (0 = default)
-    tune_visit_smem: int = 0  # schedule: KB of shared memory for shared-memory visits (0 = default, 1 = none)
+    tune_visit_smem: int = 0  # schedule: KB limit of the register-cached visits (0 = default: none)
 
     def c(self) -> msg_params:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
