@@ -119,6 +119,53 @@ int32_t sample_field(const void* prepared, int64_t npts, int32_t M, int32_t mode
                      int64_t S, void* Z, int32_t z_fp32, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Circulant-embedding sampler of the paper's own field law (Sec. 4,        */
+/* numerical experiments): Matern covariance Eq. (1.2) with distance        */
+/* r = ||T dx||, T = diag(1/sqrt(eta lambda), 1/sqrt(lambda)) R(theta)       */
+/* (Sec. 1).  Each sample draws its anisotropic ratio eta and rotation      */
+/* theta uniformly on the law's ranges (one Philox4x64-10 block, counter    */
+/* (0, s, 1, 0), key (seed, 0): u = (w >> 11) 2^-53 of words 0 and 1), so   */
+/* the eigenvalues of the embedding are recomputed for every sample:        */
+/*   c      covariance on the periodic grid of L 2^(P+1) x L 2^(Q+1) points  */
+/*          with the field's spacing, at signed periodic offsets (both signs */
+/*          averaged at an offset of exactly half the period);               */
+/*   Lambda = DFT2(c), FP64 (cuFFT D2Z);                                     */
+/*   Z      = Re DFT2(sqrt(max(Lambda, 0) / M) (xi1 + i xi2)), forward       */
+/*          transform, FP32 (cuFFT C2C), restricted to the field nodes;      */
+/*          xi1, xi2 at embedding point k are normals 2k and 2k+1 of the     */
+/*          sample's stream as msg_normals numbers them (the same 53-bit     */
+/*          uniforms; log and sin/cos in single precision).                  */
+/* Arguments:                                                               */
+/*   Z         [device] double [S][(2^(P+1)+1)(2^(Q+1)+1)], written; the    */
+/*             layout sample_field writes, ready for msg_solve_batch.        */
+/*   eta_theta [device] double [S][2] (eta, theta in radians), written, or   */
+/*             NULL.                                                         */
+/*   status    [device] int32 [S], written (0 or MSG_CE_NEGATIVE_EIGENVALUE: */
+/*             an eigenvalue below -1e-10 of the largest was set to zero,    */
+/*             L too small for the law), or NULL.                            */
+/*   workspace [device] >= ce_workspace_bytes(P, Q, law) bytes, 256-byte      */
+/*             aligned.  1 <= P, Q <= 10, S >= 0, nu in {0.5, 1.5, 2.5},      */
+/*             lambda > 0, 0 < eta_lo <= eta_hi, 2 <= L <= 64 (the periodic  */
+/*             grid holds every field node), batch >= 1.                     */
+/* Asynchronous on `stream`; the first call for a (P, Q, L, batch) creates   */
+/* and caches the cuFFT plans (which allocate device memory and block).      */
+typedef struct {
+    double nu;                 /* Matern smoothness: 0.5, 1.5 or 2.5 (closed forms of Eq. (1.2)) */
+    double lambda;             /* length scale */
+    double eta_lo, eta_hi;     /* anisotropic ratio range */
+    double theta_lo, theta_hi; /* rotation range, degrees */
+    int32_t L;                 /* periodic domain side in domain lengths (ce_padding: Sec. 4's choice) */
+    int32_t batch;             /* samples per FFT batch: the workspace grows with it */
+} msg_ce_law;
+#define MSG_CE_NEGATIVE_EIGENVALUE 1
+/* L = 1 + 2 ceil(sqrt(nu) log2(max(2^p0, 2^q0))) (Sec. 4); 0 on bad input. */
+int32_t ce_padding(double nu, int32_t p0, int32_t q0);
+size_t ce_workspace_bytes(int32_t P, int32_t Q, const msg_ce_law* law);
+int32_t ce_sample_field(int32_t P, int32_t Q, int64_t S, const msg_ce_law* law, uint64_t seed, uint64_t s0,
+                        double* Z, double* eta_theta, int32_t* status, void* workspace, size_t ws_bytes,
+                        void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* (a3)-(a13) Batched FMSG solve.                                            */
 /*                                                                          */
 /* Sample i has finest grid (P_i, Q_i) = (PQ[2i], PQ[2i+1]), 1 <= P_i, Q_i    */

@@ -63,7 +63,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    # cuFFT (the circulant-embedding sampler's transforms) from the toolkit next to nvcc
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    rpath = ["-Xlinker", "-rpath", "-Xlinker", libdir] if os.path.isdir(libdir) else []
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft", *rpath], capture_output=True,
+                       text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -17,6 +17,7 @@ enum KernelClass {
     K_NORMALS,   // Philox + Box-Muller
     K_KL,        // KL contraction
     K_MIMC,      // multi-index differences
+    K_CE,        // circulant-embedding sampler (covariance, spectrum scaling, extraction)
     K_NCLASS
 };
 

@@ -28,8 +28,11 @@ EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "m
             "msg_solve_batch", "msg_solution_values", "msg_solution", "mimc_differences",
             "mimc_differences_noalloc", "msg_device_status", "msg_last_error", "msg_version",
             "msg_launch_count",
-            "msg_profile_enable", "msg_profile_read", "msg_profile_read_level")
-KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC")
+            "msg_profile_enable", "msg_profile_read", "msg_profile_read_level",
+            "ce_padding", "ce_workspace_bytes", "ce_sample_field")
+MSG_CE_NEGATIVE_EIGENVALUE = 1
+KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC",
+                  "CE")
 
 
 class MsgError(RuntimeError):
@@ -67,6 +70,30 @@ class SolverParams:
         return msg_params(self.mu, self.nu1, self.nu2, self.max_cycles, self.eps, self.omega, self.precision,
                           self.qoi, self.coef, self.tune_block, self.tune_low_warps,
                           self.tune_low_items, self.tune_low_cut, self.tune_visit_smem)
+
+
+class msg_ce_law(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("lam", ctypes.c_double), ("eta_lo", ctypes.c_double),
+                ("eta_hi", ctypes.c_double), ("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
+                ("L", ctypes.c_int32), ("batch", ctypes.c_int32)]
+
+
+@dataclass
+class CeLaw:
+    """Field law of the paper's experiments (Sec. 4): Matern nu = 1/2, lambda = 1/4,
+    eta ~ U[1/16, 1/4], theta ~ U[-30, 30] degrees; L = 7 is ce_padding(1/2, 4, 4)."""
+    nu: float = 0.5
+    lam: float = 0.25
+    eta_lo: float = 1.0 / 16
+    eta_hi: float = 0.25
+    theta_lo: float = -30.0
+    theta_hi: float = 30.0
+    L: int = 7
+    batch: int = 8
+
+    def c(self) -> msg_ce_law:
+        return msg_ce_law(self.nu, self.lam, self.eta_lo, self.eta_hi, self.theta_lo, self.theta_hi, self.L,
+                          self.batch)
 
 
 _lib = None
@@ -121,6 +148,12 @@ def load(path: str | None = None):
     L.msg_profile_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                                    ctypes.POINTER(dbl)]
     L.msg_profile_read.restype = i32
+    L.ce_padding.argtypes = [dbl, i32, i32]
+    L.ce_padding.restype = i32
+    L.ce_workspace_bytes.argtypes = [i32, i32, ctypes.POINTER(msg_ce_law)]
+    L.ce_workspace_bytes.restype = sz
+    L.ce_sample_field.argtypes = [i32, i32, i64, ctypes.POINTER(msg_ce_law), u64, u64, vp, vp, vp, vp, sz, vp]
+    L.ce_sample_field.restype = i32
     _lib = L
     return L
 
@@ -173,6 +206,28 @@ def sample_field(prepared, npts: int, M: int, mode: int, xi, Z, stream=None):
     S = xi.shape[0]
     _check(load().sample_field(_ptr(prepared), npts, M, mode, _ptr(xi), S, _ptr(Z),
                                1 if Z.dtype == torch.float32 else 0, _stream(stream)))
+
+
+def ce_padding(nu: float, p0: int, q0: int) -> int:
+    return int(load().ce_padding(nu, p0, q0))
+
+
+def ce_workspace_bytes(P: int, Q: int, law: CeLaw) -> int:
+    c = law.c()
+    return int(load().ce_workspace_bytes(P, Q, ctypes.byref(c)))
+
+
+def ce_sample_field(P: int, Q: int, S: int, law: CeLaw, seed: int, s0: int, Z, eta_theta=None, status=None,
+                    workspace=None, stream=None):
+    """Z[S][field_points(P, Q)] (device, FP64) from the circulant-embedding sampler;
+    workspace: a device byte tensor of ce_workspace_bytes(P, Q, law) (allocated if None)."""
+    import torch
+
+    c = law.c()
+    if workspace is None:
+        workspace = torch.empty(ce_workspace_bytes(P, Q, law), dtype=torch.uint8, device=Z.device)
+    _check(load().ce_sample_field(P, Q, S, ctypes.byref(c), seed, s0, _ptr(Z), _ptr(eta_theta), _ptr(status),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def msg_workspace_bytes(PQ, prm: SolverParams) -> int:

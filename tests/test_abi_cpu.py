@@ -143,3 +143,26 @@ def test_solution_values_count_and_grid_offsets(lib):
     assert (seen == 1).all()  # the grids tile the block exactly
     with pytest.raises(msg.MsgError):
         msg.msg_solution_values([(0, 3)])
+
+
+def test_circulant_embedding_host_logic(lib):
+    """Padding (Sec. 4), workspace size, and host-side argument checks of the
+    circulant-embedding sampler; no compute call."""
+    assert msg.ce_padding(0.5, 4, 4) == 7
+    assert msg.ce_padding(1.5, 3, 5) == 15
+    assert lib.ce_padding(-1.0, 4, 4) == 0 and lib.msg_last_error() != b""
+    law = msg.CeLaw(L=7, batch=3)
+    P, Q = 3, 2
+    M1, M2 = 7 << (P + 1), 7 << (Q + 1)
+    need = 3 * (8 * M1 * M2 + 16 * M2 * (M1 // 2 + 1))
+    got = msg.ce_workspace_bytes(P, Q, law)
+    assert need <= got <= need + 3 * 256
+    assert msg.ce_workspace_bytes(P, Q, msg.CeLaw(batch=6)) > got
+    for bad in (msg.CeLaw(nu=1.0), msg.CeLaw(lam=0.0), msg.CeLaw(eta_lo=0.3, eta_hi=0.2), msg.CeLaw(L=1),
+                msg.CeLaw(batch=0), msg.CeLaw(theta_lo=10.0, theta_hi=-10.0)):
+        assert msg.ce_workspace_bytes(P, Q, bad) == 0 and lib.msg_last_error() != b""
+    assert msg.ce_workspace_bytes(0, 3, law) == 0 and msg.ce_workspace_bytes(3, 11, law) == 0
+    c = law.c()
+    assert lib.ce_sample_field(P, Q, 0, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_OK
+    assert lib.ce_sample_field(P, Q, 2, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_ERR_INVALID
+    assert lib.ce_sample_field(P, Q, -1, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_ERR_INVALID
