@@ -64,13 +64,17 @@ def parse():
                     help="also time one step of S samples through the batched path with FP64 cycles "
                          "(separates the batching gain from the precision gain; 0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass (at most --steps)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving", "ce"],
                     help="solve: the batched FMSG solve (default line); kl: KL field sampling at 1024^2 points, "
                          "M = 400, 8192 samples, every GEMM mode; uneven: 16 384 samples over grids 4..512 per "
                          "side in one call; serving: adaptive MIMC driver requests through continuous batching")
     ap.add_argument("--kl-n", type=int, default=1024, help="kl workload: points per side")
     ap.add_argument("--kl-S", type=int, default=8192, help="kl workload: samples")
     ap.add_argument("--kl-chunk", type=int, default=1024, help="kl workload: samples per call")
+    ap.add_argument("--ce-S", type=int, default=512, help="ce workload: samples")
+    ap.add_argument("--ce-batch", type=int, default=16, help="ce workload: samples per FFT batch")
+    ap.add_argument("--ce-solve-S", type=int, default=256, help="ce workload: samples also solved")
+    ap.add_argument("--ce-L", type=int, default=9, help="ce workload: periodic domain side (domain lengths)")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -584,6 +588,101 @@ def kl_workload(a):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ce workload --
+
+def ce_workload(a):
+    """The paper's own field law (Sec. 4): Matern nu = 1/2, lambda = 1/4, anisotropy
+    eta ~ U[1/16, 1/4] and rotation theta ~ U[-30, 30] degrees drawn per sample,
+    sampled exactly by circulant embedding on the (1 + 2 ceil(sqrt(nu) 4)) = 7 times
+    larger periodic domain (ce_sample_field).  Times S samples at the solve
+    workload's field shape (513 x 513 nodes for 256 x 256 grids), checks one sample
+    against the oracle, and solves a sub-batch of these fields (samples/s and
+    converged fraction of the paper's law)."""
+    import torch
+
+    import oracle
+    from oracle import circulant as oce
+    from paper_1907_12334_gb300 import build, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    P, Q, S, B, seed = a.P, a.Q, a.ce_S, min(a.ce_batch, a.ce_S), 20190729
+    # Sec. 4's padding with p0 = q0 = 4 is L = 7; at the 1/512 field spacing that leaves
+    # eigenvalues down to -2e-7 of the largest, and L = 9 removes them (the default here)
+    L = a.ce_L
+    law = msg.CeLaw(L=L, batch=B)
+    nf = msg.field_points(P, Q)
+    M1, M2 = L << (P + 1), L << (Q + 1)
+    N, H = M1 * M2, M2 * (M1 // 2 + 1)
+    ws = torch.empty(msg.ce_workspace_bytes(P, Q, law), dtype=torch.uint8, device=dev)
+    Z = torch.empty((S, nf), dtype=torch.float64, device=dev)
+    et = torch.empty((S, 2), dtype=torch.float64, device=dev)
+    st = torch.empty(S, dtype=torch.int32, device=dev)
+    msg.ce_sample_field(P, Q, B, law, seed, 0, Z, et, st, ws)  # plans, warm-up
+    torch.cuda.synchronize(dev)
+    l0 = msg.msg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler() as clk:
+        e0.record(stream)
+        msg.ce_sample_field(P, Q, S, law, seed, 0, Z, et, st, ws)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1000.0
+    launches = msg.msg_launch_count() - l0
+    # our kernels' share of the time (the rest is cuFFT): one more call with event timing
+    msg.msg_profile_enable(True, stride=1)
+    msg.ce_sample_field(P, Q, S, law, seed, 0, Z, et, st, ws)
+    torch.cuda.synchronize(dev)
+    ours = msg.msg_profile_read("CE")
+    msg.msg_profile_enable(False)
+    neg = int((st != 0).sum())
+    Zo, eta, theta, ratio = oce.ce_field(P, Q, oce.CeLaw(L=L), seed, 0)
+    err = float(np.max(np.abs(Z[0].cpu().numpy() - Zo)))
+    # algorithmic bytes of one sample: c written and read by D2Z (8N each), its half
+    # spectrum written and read (16H each), the scaled spectrum written and read by C2C
+    # and C2C's output written (8N each), the field nodes gathered and written (16 nf)
+    bytes_ps = 8.0 * N * 2 + 16.0 * H * 2 + 8.0 * N * 3 + 16.0 * nf
+    hbm, _, _ = measured_peaks()
+    gbps = bytes_ps * S / t / 1e9
+    # solve a sub-batch of these fields with the bench's solver settings
+    Ss = min(a.ce_solve_S, S)
+    prm = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, omega=a.omega)
+    PQ = np.array([[P, Q]] * Ss, dtype=np.int32)
+    wsol = torch.empty(msg.msg_workspace_bytes(PQ, prm), dtype=torch.uint8, device=dev)
+    Qo = torch.empty(Ss * P * Q, dtype=torch.float64, device=dev)
+    sst = torch.empty(Ss, dtype=torch.int32, device=dev)
+    msg.msg_solve_batch(PQ, prm, Z[:Ss].reshape(-1), Qo, sst, None, None, wsol)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    msg.msg_solve_batch(PQ, prm, Z[:Ss].reshape(-1), Qo, sst, None, None, wsol)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ts = e0.elapsed_time(e1) / 1000.0
+    conv = int((sst == 0).sum())
+    line = {
+        "metric": "circulant-embedding field samples/s", "value": S / t, "unit": "samples/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f64 eigenvalues + f32 sample transform", "data": "synthetic",
+        "config": {"workload": f"paper's field law (Sec. 4): Matern nu=1/2, lambda=1/4, eta~U[1/16,1/4], "
+                               f"theta~U[-30,30] deg per sample; {2**(P+1)+1}^2 field nodes, periodic grid "
+                               f"{M1}x{M2} (L={L}; Sec. 4's formula gives {msg.ce_padding(0.5, 4, 4)}); "
+                               f"S={S} in FFT batches of {B}", "S": S, "P": P, "Q": Q, "L": L},
+        "ms_per_sample": 1000.0 * t / S, "gpu_launches": launches, "clocks": clk.summary(),
+        "our_kernels_share": ours["ms"] / (1000.0 * t) if t > 0 else None,
+        "negative_eigenvalue_samples": neg,
+        "oracle_check": {"sample": 0, "max_abs_err": err, "eta": eta, "theta_rad": theta, "min_eig_ratio": ratio},
+        "roofline": {"bound": "hbm", "kernel": "whole sampler (our kernels + cuFFT D2Z/C2C)", "achieved": gbps,
+                     "peak": hbm, "unit": "GB/s", "frac": gbps / hbm,
+                     "algorithmic_bytes_per_sample": bytes_ps,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "solve_on_ce_fields": {"S": Ss, "samples_per_s": conv / ts, "converged": conv,
+                               "cycles_cap": a.max_cycles, "eps": a.eps},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ uneven workload --
 
 def uneven_workload(a):
@@ -795,9 +894,10 @@ def main():
     if a.impl == "reference":
         reference_arm(a, rank, world)
         return
-    if a.workload in ("kl", "uneven", "serving"):
+    if a.workload in ("kl", "uneven", "serving", "ce"):
         if rank == 0:
-            {"kl": kl_workload, "uneven": uneven_workload, "serving": serving_workload}[a.workload](a)
+            {"kl": kl_workload, "uneven": uneven_workload, "serving": serving_workload,
+             "ce": ce_workload}[a.workload](a)
         return
     if world > 1:
         import torch
