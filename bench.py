@@ -64,7 +64,7 @@ def parse():
                     help="also time one step of S samples through the batched path with FP64 cycles "
                          "(separates the batching gain from the precision gain; 0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass (at most --steps)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving", "ce"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving", "ce", "estimator"],
                     help="solve: the batched FMSG solve (default line); kl: KL field sampling at 1024^2 points, "
                          "M = 400, 8192 samples, every GEMM mode; uneven: 16 384 samples over grids 4..512 per "
                          "side in one call; serving: adaptive MIMC driver requests through continuous batching")
@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--ce-batch", type=int, default=16, help="ce workload: samples per FFT batch")
     ap.add_argument("--ce-solve-S", type=int, default=256, help="ce workload: samples also solved")
     ap.add_argument("--ce-L", type=int, default=9, help="ce workload: periodic domain side (domain lengths)")
+    ap.add_argument("--est-S", type=int, default=1024, help="estimator workload: samples at the top index")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -683,6 +684,87 @@ def ce_workload(a):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------- estimator workload --
+
+def estimator_workload(a):
+    """Sample reuse in MSG-MIMC (Sec. 3, Theorem 1) measured on the paper's own field
+    law (Sec. 4, circulant embedding, nu = 1/2, lambda = 1/4, eta and theta per
+    sample).  S samples are solved at the top index L = (K, K) of the box
+    0 <= tau <= L over the coarsest grid (p0, q0); one FMSG solve gives every
+    difference dQ_tau of the box (Eq. (3.2)).  Per QoI (Q1, Q2, Q3 of Sec. 4):
+    E_tau, V_tau over the samples; C_tau the measured work of a solve whose top
+    grid is tau (sum over its grids of cycles x p q 2^(p+q), from the solver's
+    per-grid cycle counts); rates alpha, beta, gamma fitted along each axis;
+    Theorem 1's predicted cost ratio from those rates beside the ratio of the two
+    optimal sample allocations computed from the measured V and C."""
+    import torch
+
+    from paper_1907_12334_gb300 import build, estimator as est, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p0 = q0 = 4
+    K = a.P - p0
+    P = Q = a.P
+    S, seed = a.est_S, 1907
+    law = msg.CeLaw(L=a.ce_L, batch=min(16, S))
+    nf = msg.field_points(P, Q)
+    Z = torch.empty((S, nf), dtype=torch.float64, device=dev)
+    st = torch.empty(S, dtype=torch.int32, device=dev)
+    ws = torch.empty(msg.ce_workspace_bytes(P, Q, law), dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    msg.ce_sample_field(P, Q, S, law, seed, 0, Z, None, st, ws)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_ce = e0.elapsed_time(e1) / 1000.0
+    del ws
+    PQ = np.array([[P, Q]] * S, dtype=np.int32)
+    Lb = np.array([[K, K]] * S, dtype=np.int32)
+    paper = {r.split()[0]: [float(x) for x in r.split()[1:]] for r in open(
+        os.path.join(ROOT, "tests", "golden", "table1_rates.txt")) if r.strip() and r[0] != "#"}
+    out = {}
+    t_solve = 0.0
+    for name, qoi in (("Q1", 1), ("Q2", 2), ("Q3", 3)):
+        prm = msg.SolverParams(eps=a.eps, max_cycles=a.max_cycles, qoi=qoi)
+        e0.record()
+        Qd, sst, cyc, _ = msg.solve(PQ, Z.reshape(-1), prm)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t_solve += e0.elapsed_time(e1) / 1000.0
+        ok = (sst == 0).cpu().numpy()
+        dQ = torch.empty(S * (K + 1) * (K + 1), dtype=torch.float64, device=dev)
+        msg.mimc_differences(Lb, p0, q0, Qd, dQ)
+        torch.cuda.synchronize(dev)
+        d = dQ.cpu().numpy().reshape(S, K + 1, K + 1)[ok]
+        c = cyc.cpu().numpy().reshape(S, P, Q)[ok].astype(np.float64)
+        E, V = d.mean(0), d.var(0, ddof=1)
+        # work of one grid solve: its cycles x p q 2^(p+q) (a W-cycle over its hierarchy)
+        pp, qq = np.meshgrid(np.arange(1, P + 1), np.arange(1, Q + 1), indexing="ij")
+        w = c.mean(0) * pp * qq * 2.0 ** (pp + qq)
+        C = np.array([[w[: p0 + l1, : q0 + l2].sum() for l2 in range(K + 1)] for l1 in range(K + 1)])
+        r = est.rates(E, V, C)
+        no, yes, N, Nr = est.costs(V, C, tol=1e-3)
+        pr = paper[name]
+        out[name] = {"converged": int(ok.sum()), "alpha": r["alpha"], "beta": r["beta"], "gamma": r["gamma"],
+                     "theorem1_ratio_fitted_rates": est.theorem1_ratio(r["beta"], r["gamma"]),
+                     "allocation_ratio_measured_V_C": yes / no,
+                     "negative_reuse_allocations": int((Nr < 0).sum()),
+                     "paper_table1": {"alpha": pr[0:2], "beta": pr[2:4], "gamma": pr[4:6],
+                                      "theorem1_ratio": est.theorem1_ratio(pr[2:4], pr[4:6])},
+                     "E": E.tolist(), "V": V.tolist()}
+    line = {"metric": "MSG-MIMC sample-reuse cost ratio (Theorem 1)", "value": out["Q3"]["allocation_ratio_measured_V_C"],
+            "unit": "cost with reuse / without", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"paper's field law (Sec. 4, circulant embedding L={a.ce_L}), S={S} samples at "
+                                   f"the top index L=({K},{K}) over p0=q0={p0} (grids up to {2**P}x{2**Q}), "
+                                   f"Q1/Q2/Q3, eps={a.eps}", "S": S, "K": K, "p0": p0},
+            "seconds": {"sampling": t_ce, "solves": t_solve}, "qoi": out}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ uneven workload --
 
 def uneven_workload(a):
@@ -894,10 +976,10 @@ def main():
     if a.impl == "reference":
         reference_arm(a, rank, world)
         return
-    if a.workload in ("kl", "uneven", "serving", "ce"):
+    if a.workload in ("kl", "uneven", "serving", "ce", "estimator"):
         if rank == 0:
             {"kl": kl_workload, "uneven": uneven_workload, "serving": serving_workload,
-             "ce": ce_workload}[a.workload](a)
+             "ce": ce_workload, "estimator": estimator_workload}[a.workload](a)
         return
     if world > 1:
         import torch
