@@ -81,6 +81,8 @@ def lib():
             L.orc_grid_qoi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
             L.orc_hier_cycles.argtypes = [ctypes.c_void_p, _ip, _dp]
             L.orc_grid_coef.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.orc_cycle_history.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_std_block.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
             _lib = L
     return _lib
 
@@ -227,6 +229,28 @@ class Hierarchy:
         a = np.ascontiguousarray(arr, dtype=np.float64)
         assert a.shape == self.shape(p, q)
         assert lib().orc_grid_set(self.h, p, q, which, _d(a)) == 0
+
+    def cycle_history(self, method: int, ncycles: int) -> np.ndarray:
+        """||r_k||/||b|| on the finest grid after k = 0..ncycles cycles from u = 0, b = 1;
+        method 0: MSG cycles (Algorithm 1), 1: standard coarsening."""
+        h = np.empty(ncycles + 1)
+        assert lib().orc_cycle_history(self.h, method, ncycles, _d(h)) == 0
+        return h
+
+    def std_restrict(self, p, q, f):
+        out = np.empty(self.shape(p - 1, q - 1))
+        assert lib().orc_std_block(self.h, p, q, 0, _d(np.ascontiguousarray(f, dtype=np.float64)), _d(out)) == 0
+        return out
+
+    def std_prolong(self, p, q, e):
+        out = np.empty(self.shape(p, q))
+        assert lib().orc_std_block(self.h, p, q, 1, _d(np.ascontiguousarray(e, dtype=np.float64)), _d(out)) == 0
+        return out
+
+    def line_solve(self, p, q, b):
+        out = np.empty(self.shape(p, q))
+        assert lib().orc_std_block(self.h, p, q, 2, _d(np.ascontiguousarray(b, dtype=np.float64)), _d(out)) == 0
+        return out
 
     def coef(self, p, q):
         """(ax [(ny+1)][nx], ay [ny][nx+1]): a at the x- and y-face midpoints of grid (p,q)."""

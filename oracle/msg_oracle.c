@@ -823,3 +823,125 @@ int orc_grid_coef(ohier* H, int p, int q, double* ax, double* ay)
     memcpy(ay, g->ay, sizeof(double) * (g->nx + 1) * g->ny);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Convergence study (Sec. 2, numerical experiments: residual norms over     */
+/* W-cycles from a zero initial guess, MSG against multigrid with standard   */
+/* coarsening).                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* READING: the paper does not give the transfer operators of its "classic MG".
+ * The textbook ones for vertex-centred grids are used: full weighting, the
+ * tensor product of 1/4 [1 2 1] in x and y, from (p,q) to (p-1,q-1), and
+ * bilinear interpolation back; the coarse operators are the direct
+ * discretisations on the diagonal grids (P-k, Q-k) of the MSG hierarchy (the
+ * same coefficients), with the same red-black smoother and damping.  Coarsening
+ * stops at the first grid with a single interior line (p = 1 or q = 1), solved
+ * exactly. */
+static double Rfw_at(const ogrid* f, const double* r, int ic, int jc)
+{
+    int W = f->nx + 1, c = 2 * jc * W + 2 * ic;
+    double edge = r[c - 1] + r[c + 1] + r[c - W] + r[c + W];
+    double corner = r[c - W - 1] + r[c - W + 1] + r[c + W - 1] + r[c + W + 1];
+    return (4.0 * r[c] + 2.0 * edge + corner) / 16.0;
+}
+
+/* bilinear interpolation from (p-1,q-1) to fine node (i,j) of (p,q) */
+static double Pbl_at(const ogrid* co, const double* v, int i, int j)
+{
+    int W = co->nx + 1, i0 = i / 2, j0 = j / 2;
+    if (!(i & 1) && !(j & 1)) return v[j0 * W + i0];
+    if ((i & 1) && !(j & 1)) return 0.5 * (v[j0 * W + i0] + v[j0 * W + i0 + 1]);
+    if (!(i & 1) && (j & 1)) return 0.5 * (v[j0 * W + i0] + v[(j0 + 1) * W + i0]);
+    return 0.25 * (v[j0 * W + i0] + v[j0 * W + i0 + 1] + v[(j0 + 1) * W + i0] + v[(j0 + 1) * W + i0 + 1]);
+}
+
+/* exact solve of A u = b on a grid with one interior line (Thomas algorithm) */
+static void line_solve(ogrid* g)
+{
+    const int row = g->ny == 2; /* one interior row (else one interior column) */
+    const int n = row ? g->nx - 1 : g->ny - 1, W = g->nx + 1;
+    double* cp = (double*)calloc((size_t)n + 1, sizeof(double));
+    double* dp = (double*)calloc((size_t)n + 1, sizeof(double));
+    for (int k = 0; k < n; ++k) {
+        int i = row ? k + 1 : 1, j = row ? 1 : k + 1, c = j * W + i;
+        double lo, up; /* couplings to the previous and next unknown of the line */
+        if (row) { lo = -g->ax[j * g->nx + i - 1] / (g->dx * g->dx); up = -g->ax[j * g->nx + i] / (g->dx * g->dx); }
+        else { lo = -g->ay[(j - 1) * W + i] / (g->dy * g->dy); up = -g->ay[j * W + i] / (g->dy * g->dy); }
+        double d = diag_at(g, i, j) - (k > 0 ? lo * cp[k - 1] : 0.0);
+        cp[k] = up / d;
+        dp[k] = (g->b[c] - (k > 0 ? lo * dp[k - 1] : 0.0)) / d;
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        int i = row ? k + 1 : 1, j = row ? 1 : k + 1;
+        double next = k + 1 < n ? g->u[row ? j * W + i + 1 : (j + 1) * W + i] : 0.0;
+        g->u[j * W + i] = dp[k] - cp[k] * next;
+    }
+    free(cp);
+    free(dp);
+}
+
+static void std_cycle(ohier* H, int p, int q)
+{
+    ogrid* g = G(H, p, q);
+    if (p == 1 || q == 1) { line_solve(g); return; }
+    for (int k = 0; k < H->nu1; ++k) smooth_rbgs(g);
+    residual(g);
+    ogrid* co = G(H, p - 1, q - 1);
+    memset(co->b, 0, sizeof(double) * nodes(co));
+    memset(co->u, 0, sizeof(double) * nodes(co));
+    for (int jc = 1; jc < co->ny; ++jc)
+        for (int ic = 1; ic < co->nx; ++ic) co->b[jc * (co->nx + 1) + ic] = Rfw_at(g, g->r, ic, jc);
+    for (int k = 0; k < H->mu; ++k) std_cycle(H, p - 1, q - 1);
+    for (int j = 1; j < g->ny; ++j)
+        for (int i = 1; i < g->nx; ++i) g->u[j * (g->nx + 1) + i] += H->omega * Pbl_at(co, co->u, i, j);
+    for (int k = 0; k < H->nu2; ++k) smooth_rbgs(g);
+}
+
+/* hist[k] = ||b - A u_k||_h / ||b||_h on the finest grid after k cycles from
+ * u_0 = 0 with b = 1 (hist[0] = 1); method 0: MSG (Algorithm 1 over the whole
+ * hierarchy), 1: standard coarsening. */
+int orc_cycle_history(ohier* H, int method, int ncycles, double* hist)
+{
+    ogrid* g = G(H, H->P, H->Q);
+    H->Pa = H->P;
+    H->Qa = H->Q;
+    orc_hier_set_rhs(H, NULL);
+    memset(g->u, 0, sizeof(double) * nodes(g));
+    hist[0] = grid_relres(g);
+    for (int k = 1; k <= ncycles; ++k) {
+        if (method == 0) orc_mu_cycle(H, H->P + H->Q - 2);
+        else std_cycle(H, H->P, H->Q);
+        hist[k] = grid_relres(g);
+    }
+    return 0;
+}
+
+/* Building blocks for the pins: which 0: out = full weighting of `in` (grid
+ * (p,q)) on (p-1,q-1); 1: out = bilinear interpolation of `in` (grid
+ * (p-1,q-1)) on (p,q); 2: exact line solve on (p,q) with b = in, out = u. */
+int orc_std_block(ohier* H, int p, int q, int which, const double* in, double* out)
+{
+    ogrid* g = grid_checked(H, p, q);
+    if (!g) return -1;
+    if (which == 2) {
+        if (p != 1 && q != 1) return -1;
+        memcpy(g->b, in, sizeof(double) * nodes(g));
+        memset(g->u, 0, sizeof(double) * nodes(g));
+        line_solve(g);
+        memcpy(out, g->u, sizeof(double) * nodes(g));
+        return 0;
+    }
+    if (p < 2 || q < 2) return -1;
+    ogrid* co = G(H, p - 1, q - 1);
+    if (which == 0) {
+        memset(out, 0, sizeof(double) * nodes(co));
+        for (int jc = 1; jc < co->ny; ++jc)
+            for (int ic = 1; ic < co->nx; ++ic) out[jc * (co->nx + 1) + ic] = Rfw_at(g, in, ic, jc);
+    } else {
+        memset(out, 0, sizeof(double) * nodes(g));
+        for (int j = 1; j < g->ny; ++j)
+            for (int i = 1; i < g->nx; ++i) out[j * (g->nx + 1) + i] = Pbl_at(co, in, i, j);
+    }
+    return 0;
+}

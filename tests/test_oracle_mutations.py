@@ -43,6 +43,14 @@ MUTATIONS = [
      "while (!(rr <= H->eps) && n < H->max_cycles && rr == rr && rr <= 1.0);", "keeps_cycling"),
     ("box-muller radius", "double rad = sqrt(-2.0 * log(1.0 - ua));", "double rad = sqrt(-1.0 * log(1.0 - ua));",
      "normals_distribution"),
+    ("standard restriction corner weight", "return (4.0 * r[c] + 2.0 * edge + corner) / 16.0;",
+     "return (4.0 * r[c] + 2.0 * edge + 2.0 * corner) / 16.0;", "std_transfer"),
+    ("bilinear cell-centre weight",
+     "return 0.25 * (v[j0 * W + i0] + v[j0 * W + i0 + 1] + v[(j0 + 1) * W + i0] + v[(j0 + 1) * W + i0 + 1]);",
+     "return 0.25 * (v[j0 * W + i0] + v[j0 * W + i0 + 1] + v[(j0 + 1) * W + i0] + v[(j0 + 1) * W + i0]);",
+     "std_transfer"),
+    ("line solve elimination", "double d = diag_at(g, i, j) - (k > 0 ? lo * cp[k - 1] : 0.0);",
+     "double d = diag_at(g, i, j);", "line_solve"),
 ]
 
 

@@ -495,3 +495,64 @@ def test_theorem1_cost_ratio_from_table1():
     assert ratios["Q2"] == pytest.approx(0.515, abs=1e-3)
     assert ratios["Q3"] == pytest.approx(0.387, abs=1e-3)
     assert ratios["Q3"] < ratios["Q2"] < ratios["Q1"]  # largest benefit for Q3 (Sec. 4)
+
+
+# ----------------------------------------------- convergence study (Sec. 2) --
+
+def test_std_transfer_adjoint():
+    """Full weighting is 1/4 of the transpose of bilinear interpolation on
+    vertex-centred grids: 4 <R f, e>_coarse = <f, P e>_fine over interior nodes,
+    for random f and e (a wrong stencil weight breaks it)."""
+    rng = np.random.default_rng(3)
+    for P, Q in [(3, 3), (4, 2), (2, 5)]:
+        H = oracle.Hierarchy(P, Q)
+        f = np.zeros(H.shape(P, Q))
+        f[1:-1, 1:-1] = rng.standard_normal((f.shape[0] - 2, f.shape[1] - 2))
+        e = np.zeros(H.shape(P - 1, Q - 1))
+        e[1:-1, 1:-1] = rng.standard_normal((e.shape[0] - 2, e.shape[1] - 2))
+        Rf, Pe = H.std_restrict(P, Q, f), H.std_prolong(P, Q, e)
+        assert 4.0 * np.sum(Rf * e) == pytest.approx(np.sum(f * Pe), rel=1e-13)
+        # interpolation reproduces bilinear functions exactly (and restriction preserves constants inside)
+        yy, xx = np.meshgrid(np.arange(e.shape[0]) / (e.shape[0] - 1), np.arange(e.shape[1]) / (e.shape[1] - 1),
+                             indexing="ij")
+        lin = 1.0 + 2.0 * xx - 3.0 * yy + 0.5 * xx * yy
+        yf, xf = np.meshgrid(np.arange(f.shape[0]) / (f.shape[0] - 1), np.arange(f.shape[1]) / (f.shape[1] - 1),
+                             indexing="ij")
+        np.testing.assert_allclose(H.std_prolong(P, Q, lin)[1:-1, 1:-1],
+                                   (1.0 + 2.0 * xf - 3.0 * yf + 0.5 * xf * yf)[1:-1, 1:-1], rtol=1e-14)
+
+
+def test_std_line_solve_is_exact():
+    """The coarsest standard-coarsening grid (one interior line) is solved exactly."""
+    rng = np.random.default_rng(5)
+    law = inputs.small_law(16)
+    for P, Q, p, q in [(4, 3, 1, 3), (4, 3, 4, 1), (2, 2, 1, 1)]:
+        Phi, sl = inputs.kl_basis(P, Q, law)
+        H = oracle.Hierarchy(P, Q, Z=oracle.kl_field(Phi, sl, rng.standard_normal(16)))
+        b = np.zeros(H.shape(p, q))
+        b[1:-1, 1:-1] = rng.standard_normal((b.shape[0] - 2, b.shape[1] - 2))
+        u = H.line_solve(p, q, b)
+        Au = H.apply(p, q, u)
+        np.testing.assert_allclose(Au[1:-1, 1:-1], b[1:-1, 1:-1], rtol=1e-12, atol=1e-12 * np.abs(b).max())
+
+
+def test_std_convergence_textbook_poisson():
+    """a = 1 on square grids: the standard-coarsening W(2,2) cycle with red-black
+    Gauss-Seidel reduces the residual by well under 0.1 per cycle (textbook
+    behaviour) and reaches the rounding floor, i.e. its fixed point is A^-1 b."""
+    for P in (3, 5, 6):
+        h = oracle.Hierarchy(P, P).cycle_history(1, 40)
+        rho = (h[8] / h[0]) ** (1 / 8)
+        assert rho < 0.1, (P, rho)
+        assert h[-1] < 1e-12
+
+
+def test_msg_robust_where_std_coarsening_degrades():
+    """Sec. 2: multigrid with standard coarsening and a point smoother degrades
+    on anisotropic problems; MSG does not.  With a = 1 on 64 x 4 cells (couplings
+    256:1) the standard cycle's rate is poor while MSG's stays small."""
+    H = oracle.Hierarchy(6, 2)
+    hs, hm = H.cycle_history(1, 10), H.cycle_history(0, 10)
+    rho_s = (hs[10] / hs[0]) ** 0.1
+    rho_m = (hm[6] / hm[0]) ** (1 / 6)
+    assert rho_s > 0.4 and rho_m < 0.1, (rho_s, rho_m)
