@@ -21,7 +21,8 @@
  *     before the call returns (their contents go through the library's own
  *     pinned staging).  Exceptions: msg_solve_batch synchronises `stream` while
  *     it runs (its schedule reads per-step convergence counts on the host), and
- *     mimc_differences_noalloc returns after its work has finished;
+ *     mimc_differences_noalloc and msg_cycle_history return after their work
+ *     has finished;
  *   - the return value is MSG_OK or an error code; on error
  *     msg_last_error() returns a description (thread-local string);
  *   - no entry point traps or aborts; per-sample numerical failures are
@@ -208,6 +209,28 @@ int32_t msg_solve_batch(const int32_t* PQ, int64_t S, const msg_params* prm, con
 int64_t msg_solution_values(const int32_t* PQ, int64_t S);
 int32_t msg_solution(const int32_t* PQ, int64_t S, const msg_params* prm, const void* workspace, size_t ws_bytes,
                      double* u_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Convergence study (Sec. 2, numerical experiments): residual history of     */
+/* plain cycles from u = 0 with b = 1 on the finest grid (P, Q) of S samples   */
+/* of one shape, in FP64 (prm->precision is not used):                        */
+/*   MSG_HIST_MSG       MSG mu-cycles (Algorithm 1 over the whole hierarchy);  */
+/*   MSG_HIST_STANDARD  multigrid with standard coarsening on the grids        */
+/*                      (P-k, Q-k) of the same hierarchy: full weighting,      */
+/*                      bilinear interpolation, the same smoother, damping and */
+/*                      coefficients, exact solve of the first grid with one   */
+/*                      interior line.                                         */
+/*   Z    [device] double [S][field_points(P, Q)], read.                      */
+/*   hist [device] double [S][ncycles + 1], written: ||1 - A u_k||_h / ||1||_h */
+/*        after k cycles (hist[s][0] = 1).                                     */
+/*   workspace [device] >= msg_history_workspace_bytes(P, Q, S, prm, method), */
+/*        256-byte aligned.  1 <= P, Q <= 10, 1 <= ncycles <= 1000.            */
+/* msg_cycle_history returns once its work has finished.                      */
+#define MSG_HIST_MSG 0
+#define MSG_HIST_STANDARD 1
+size_t msg_history_workspace_bytes(int32_t P, int32_t Q, int64_t S, const msg_params* prm, int32_t method);
+int32_t msg_cycle_history(int32_t P, int32_t Q, int64_t S, const msg_params* prm, int32_t method, const double* Z,
+                          int32_t ncycles, double* hist, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* (a14) Multi-index differences (Sec. 3, Eq. (3.2)) and Y (Eq. (3.6)).       */

@@ -415,6 +415,169 @@ __global__ void k_post(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* a
     visit_post(CtaGroup(), h, t.seg->p, t.seg->q, nu2, (T)omega);
 }
 
+// ------------------------------------------------------ convergence study --
+//
+// Residual history of plain cycles from a zero initial guess on each sample's
+// finest grid, b = 1 (Sec. 2, numerical experiments): MSG cycles (Algorithm 1
+// over the whole hierarchy, by the visit halves above), or multigrid with
+// standard coarsening on the diagonal grids (P-k, Q-k) of the same hierarchy:
+// full weighting (the tensor product of 1/4 [1 2 1]), bilinear interpolation,
+// the same red-black smoother, coefficients and damping, and an exact solve
+// of the first grid with a single interior line (p = 1 or q = 1).  The paper
+// does not give its standard-coarsening operators; these are the textbook ones
+// for vertex-centred grids.  One CTA per sample runs a host-built program of
+// the cycle's operations, in FP64.
+
+enum HistOp { H_PRE = 0, H_POST, H_STD_PRE, H_STD_POST, H_STD_LINE };
+
+// nu1 sweeps, r = b - A u into the grid's by plane (free in this method), full
+// weighting into the child's bx, child u = 0.
+template <class T, class G>
+__device__ void cta_std_pre(const G& grp, const Hier<T>& h, int p, int q, int nu1)
+{
+    GView<T> g = view_of(h, p, q);
+    g.bmode = 0;
+    cta_smooth(grp, g, nu1);
+    const int W = g.nx + 1, n = (g.ny - 1) * W;
+    T* r = h.sby + h.scr + grid_offset(p, q, h.qi);
+    for (int k = grp.tid; k < n; k += grp.n) {
+        const int c = W + k, i = c % W;
+        if (i == 0 || i == g.nx) continue;
+        r[c] = res_at(g, c, W);
+    }
+    grp.sync();
+    const int ncx = g.nx >> 1, ncy = g.ny >> 1, Wc = ncx + 1;
+    T* cb = h.sbx + h.scr + grid_offset(p - 1, q - 1, h.qi);
+    T* cu = h.su + h.scr + grid_offset(p - 1, q - 1, h.qi);
+    for (int k = grp.tid; k < Wc * (ncy + 1); k += grp.n) {
+        const int jc = k / Wc, ic = k - jc * Wc;
+        cu[k] = T(0);
+        if (ic == 0 || ic == ncx || jc == 0 || jc == ncy) continue;
+        const int c = 2 * jc * W + 2 * ic;
+        const T edge = r[c - 1] + r[c + 1] + r[c - W] + r[c + W];
+        const T corner = r[c - W - 1] + r[c - W + 1] + r[c + W - 1] + r[c + W + 1];
+        cb[k] = (T(4) * r[c] + T(2) * edge + corner) / T(16);
+    }
+    grp.sync();
+}
+
+// u += omega * bilinear(child u), then nu2 sweeps.
+template <class T, class G>
+__device__ void cta_std_post(const G& grp, const Hier<T>& h, int p, int q, int nu2, T omega)
+{
+    GView<T> g = view_of(h, p, q);
+    g.bmode = 0;
+    const T* cu = h.su + h.scr + grid_offset(p - 1, q - 1, h.qi);
+    const int W = g.nx + 1, Wc = (g.nx >> 1) + 1, n = (g.ny - 1) * W;
+    for (int k = grp.tid; k < n; k += grp.n) {
+        const int c = W + k, j = c / W, i = c - j * W;
+        if (i == 0 || i == g.nx) continue;
+        const int b0 = (j >> 1) * Wc + (i >> 1);
+        T v;
+        if (!(i & 1) && !(j & 1)) v = cu[b0];
+        else if (!(j & 1)) v = T(0.5) * (cu[b0] + cu[b0 + 1]);
+        else if (!(i & 1)) v = T(0.5) * (cu[b0] + cu[b0 + Wc]);
+        else v = T(0.25) * (cu[b0] + cu[b0 + 1] + cu[b0 + Wc] + cu[b0 + Wc + 1]);
+        g.u[c] += omega * v;
+    }
+    grp.sync();
+    cta_smooth(grp, g, nu2);
+}
+
+// Exact solve on a grid with one interior line (Thomas algorithm, one thread;
+// the by plane holds the elimination coefficients).
+template <class T, class G>
+__device__ void cta_std_line(const G& grp, const Hier<T>& h, int p, int q)
+{
+    GView<T> g = view_of(h, p, q);
+    g.bmode = 0;
+    T* e = h.sby + h.scr + grid_offset(p, q, h.qi);
+    const int W = g.nx + 1, row = g.ny == 2, n = row ? g.nx - 1 : g.ny - 1;
+    for (int k = grp.tid; k < W * (g.ny + 1); k += grp.n) g.u[k] = T(0);
+    grp.sync();
+    if (grp.tid == 0) {
+        T cprev = T(0), dprev = T(0);
+        for (int k = 0; k < n; ++k) {
+            const int c = row ? W + k + 1 : (k + 1) * W + 1;
+            const T aw = g.ax[c - 1], ae = g.ax[c], as = g.ay[c - W], an = g.ay[c];
+            const T lo = row ? -aw : -as, up = row ? -ae : -an;
+            const T d = (aw + ae + as + an) - (k > 0 ? lo * cprev : T(0));
+            cprev = up / d;
+            dprev = (g.bx[c] - (k > 0 ? lo * dprev : T(0))) / d;
+            e[2 * k] = cprev;
+            e[2 * k + 1] = dprev;
+        }
+        T next = T(0);
+        for (int k = n - 1; k >= 0; --k) {
+            const int c = row ? W + k + 1 : (k + 1) * W + 1;
+            next = e[2 * k + 1] - e[2 * k] * next;
+            g.u[c] = next;
+        }
+    }
+    grp.sync();
+}
+
+// hist[s][k] = ||1 - A u_k||_h / ||1||_h on the sample's finest grid, k = 0..ncycles.
+// prog: one cycle, op.x = kind | (p or diagonal) << 4 | q << 12, op.y = zero-init.
+template <class T>
+__global__ void k_cycle_history(DevCtx cx, T* su, T* sbx, T* sby, const T* ax, const T* ay, const int2* prog,
+                                int nops, int ncycles, CycleParams cp, int band, double* hist)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // `band` residual nodes of the MSG restriction
+    __shared__ double red[32];
+    TaskRef t;
+    if (!resolve_2d(cx, t)) return;
+    const Hier<T> h = hier_of(cx, t, su, sbx, sby, ax, ay);
+    const CtaGroup grp;
+    const int P = h.pi, Q = h.qi;
+    const GView<T> top = view_of(h, P, Q);  // no parents: b = bx
+    const int W = top.nx + 1, n = W * (top.ny + 1);
+    T* bx = h.sbx + h.scr + grid_offset(P, Q, Q);
+    for (int k = grp.tid; k < n; k += grp.n) {
+        const int j = k / W, i = k - j * W;
+        top.u[k] = T(0);
+        bx[k] = (i > 0 && i < top.nx && j > 0 && j < top.ny) ? T(1) : T(0);
+    }
+    grp.sync();
+    double* hs = hist + (int64_t)t.s * (ncycles + 1);
+    const double nb = sqrt((double)(top.nx - 1) * (top.ny - 1));
+    for (int cyc = 0; cyc <= ncycles; ++cyc) {
+        if (cyc > 0)
+            for (int o = 0; o < nops; ++o) {
+                const int2 op = prog[o];
+                const int kind = op.x & 15, a = (op.x >> 4) & 255, b = (op.x >> 12) & 255;
+                if (kind == H_PRE || kind == H_POST) {
+                    for (int p = max(1, a + 2 - Q); p <= min(P, a + 1); ++p) {
+                        if (kind == H_PRE) visit_pre(grp, h, p, a + 2 - p, op.y, cp.nu1, (T*)smem_raw, band);
+                        else visit_post(grp, h, p, a + 2 - p, cp.nu2, (T)cp.omega);
+                    }
+                } else if (kind == H_STD_PRE) {
+                    cta_std_pre(grp, h, a, b, cp.nu1);
+                } else if (kind == H_STD_POST) {
+                    cta_std_post(grp, h, a, b, cp.nu2, (T)cp.omega);
+                } else {
+                    cta_std_line(grp, h, a, b);
+                }
+            }
+        double s = 0.0;
+        for (int k = grp.tid; k < (top.ny - 1) * W; k += grp.n) {
+            const int c = W + k, i = c % W;
+            if (i == 0 || i == top.nx) continue;
+            const double r = (double)res_at(top, c, W);
+            s += r * r;
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((grp.tid & 31) == 0) red[grp.tid >> 5] = s;
+        grp.sync();
+        if (grp.tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (grp.n + 31) / 32; ++w) tot += red[w];
+            hs[cyc] = sqrt(tot) / nb;
+        }
+        grp.sync();
+    }
+}
+
 // --------------------------------------------- register-cached visits --
 //
 // Full launches of the global-memory visits above are bound by instruction
@@ -2477,6 +2640,75 @@ static int run_solve(const Plan& pl, const WsLayout& wl, char* ws, const msg_par
     return MSG_OK;
 }
 
+// ------------------------------------------------- convergence study (host) --
+namespace {
+
+void hist_prog_msg(int s, int zi, int mu, std::vector<int2>& prog)
+{
+    prog.push_back(make_int2(H_PRE | s << 4, zi));
+    if (s == 0) return;
+    for (int k = 0; k < mu; ++k) hist_prog_msg(s - 1, k == 0, mu, prog);
+    prog.push_back(make_int2(H_POST | s << 4, 0));
+}
+
+void hist_prog_std(int p, int q, int mu, std::vector<int2>& prog)
+{
+    if (p == 1 || q == 1) {
+        prog.push_back(make_int2(H_STD_LINE | p << 4 | q << 12, 0));
+        return;
+    }
+    prog.push_back(make_int2(H_STD_PRE | p << 4 | q << 12, 0));
+    for (int k = 0; k < mu; ++k) hist_prog_std(p - 1, q - 1, mu, prog);
+    prog.push_back(make_int2(H_STD_POST | p << 4 | q << 12, 0));
+}
+
+std::vector<int2> hist_prog(int P, int Q, int method, int mu)
+{
+    std::vector<int2> prog;
+    if (method == 0) hist_prog_msg(P + Q - 2, 0, mu, prog);  // the top keeps its iterate
+    else hist_prog_std(P, Q, mu, prog);
+    return prog;
+}
+
+struct HistLayout {
+    size_t samples, gpos, slist, groups, segs, prog, ax, ay, su, sbx, sby, total;
+};
+
+HistLayout hist_layout(int P, int Q, int64_t S, size_t nprog)
+{
+    HistLayout w;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += (b + 255) / 256 * 256; return o; };
+    const size_t R = (size_t)rect_nodes(P, Q) * (size_t)S;
+    w.samples = take(sizeof(SampleInfo) * S);
+    w.gpos = take(sizeof(int) * S);
+    w.slist = take(sizeof(int) * S);
+    w.groups = take(sizeof(Group));
+    w.segs = take(sizeof(Segment) * (P * Q + 1));
+    w.prog = take(sizeof(int2) * nprog);
+    w.ax = take(sizeof(double) * R);
+    w.ay = take(sizeof(double) * R);
+    w.su = take(sizeof(double) * R);
+    w.sbx = take(sizeof(double) * R);
+    w.sby = take(sizeof(double) * R);
+    w.total = off;
+    return w;
+}
+
+int hist_check(int P, int Q, int64_t S, const msg_params* prm, int method, int ncycles)
+{
+    const int32_t pq[2] = {P, Q};
+    int rc = validate(pq, 1, prm);
+    if (rc != MSG_OK) return rc;
+    if (P > 10 || Q > 10) { set_error("history: P, Q <= 10"); return MSG_ERR_INVALID; }
+    if (S < 0) { set_error("S < 0"); return MSG_ERR_INVALID; }
+    if (method != MSG_HIST_MSG && method != MSG_HIST_STANDARD) { set_error("method must be MSG_HIST_MSG or MSG_HIST_STANDARD"); return MSG_ERR_INVALID; }
+    if (ncycles < 1 || ncycles > 1000) { set_error("ncycles must be in [1, 1000]"); return MSG_ERR_INVALID; }
+    return MSG_OK;
+}
+
+}  // namespace
+
 }  // namespace msg
 
 using namespace msg;
@@ -2549,4 +2781,78 @@ extern "C" int64_t msg_solution_values(const int32_t* PQ, int64_t S)
         n += rect_nodes(PQ[2 * i], PQ[2 * i + 1]);
     }
     return n;
+}
+
+extern "C" size_t msg_history_workspace_bytes(int32_t P, int32_t Q, int64_t S, const msg_params* prm, int32_t method)
+{
+    clear_error();
+    if (hist_check(P, Q, S, prm, method, 1) != MSG_OK) return 0;
+    return hist_layout(P, Q, S, hist_prog(P, Q, method, prm->mu).size()).total;
+}
+
+extern "C" int32_t msg_cycle_history(int32_t P, int32_t Q, int64_t S, const msg_params* prm, int32_t method,
+                                     const double* Z, int32_t ncycles, double* hist, void* workspace, size_t ws_bytes,
+                                     void* stream)
+{
+    clear_error();
+    int rc = hist_check(P, Q, S, prm, method, ncycles);
+    if (rc != MSG_OK) return rc;
+    if (S == 0) return MSG_OK;
+    if (!Z || !hist || !workspace) { set_error("Z, hist or workspace is NULL"); return MSG_ERR_INVALID; }
+    if ((uintptr_t)workspace % 256) { set_error("workspace must be 256-byte aligned"); return MSG_ERR_INVALID; }
+    const std::vector<int2> prog = hist_prog(P, Q, method, prm->mu);
+    const HistLayout w = hist_layout(P, Q, S, prog.size());
+    if (ws_bytes < w.total) {
+        set_error("workspace too small: need " + std::to_string(w.total) + " bytes");
+        return MSG_ERR_WORKSPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const int64_t R = rect_nodes(P, Q), nf = field_nodes(P, Q);
+    // one group, one sample list; segments: every grid (coefficients), then the top item (cycles)
+    std::vector<SampleInfo> samples(S);
+    std::vector<int> ids(S);
+    for (int64_t s = 0; s < S; ++s) {
+        samples[s] = SampleInfo{P, Q, s * R, s * nf, 0};
+        ids[s] = (int)s;
+    }
+    const Group grp{P, Q, 0, (int)S, 0, R};
+    std::vector<Segment> segs;
+    for (int p = 1; p <= P; ++p)
+        for (int q = 1; q <= Q; ++q)
+            segs.push_back(Segment{0, P, Q, p, q, (int64_t)segs.size() * S, S, 0, 0, 0});
+    segs.push_back(Segment{0, P, Q, P, Q, 0, S, 0, 0, 0});
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.samples, samples.data(), sizeof(SampleInfo) * S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.gpos, ids.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.slist, ids.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.groups, &grp, sizeof(Group), cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.segs, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, st));
+    MSG_CUDA_TRY(cudaMemcpyAsync(ws + w.prog, prog.data(), sizeof(int2) * prog.size(), cudaMemcpyHostToDevice, st));
+    DevCtx cx;
+    cx.samples = (const SampleInfo*)(ws + w.samples);
+    cx.gpos = (const int*)(ws + w.gpos);
+    cx.slist = (const int*)(ws + w.slist);
+    cx.groups = (const Group*)(ws + w.groups);
+    cx.segs = (const Segment*)(ws + w.segs);
+    cx.nseg = P * Q;
+    double* ax = (double*)(ws + w.ax);
+    double* ay = (double*)(ws + w.ay);
+    prof_begin(K_COEFFS, st);
+    k_coeffs<<<(unsigned)(P * Q * S), kThreads, 0, st>>>(cx, Z, prm->coef, ax, ay, nullptr, nullptr);
+    prof_end(K_COEFFS, st, (double)S * R * 32.0, 0.0);
+    MSG_CHECK_LAUNCH();
+    DevCtx ch = cx;
+    ch.segs = cx.segs + P * Q;
+    ch.nseg = 1;
+    const int band = std::max(kBandNodes, 3 * ((1 << P) + 1));
+    const CycleParams cp{prm->mu, prm->nu1, prm->nu2, prm->omega};
+    prof_begin(K_PRE, st);
+    k_cycle_history<double><<<dim3((unsigned)S, 1), 256, sizeof(double) * band, st>>>(
+        ch, (double*)(ws + w.su), (double*)(ws + w.sbx), (double*)(ws + w.sby), ax, ay,
+        (const int2*)(ws + w.prog), (int)prog.size(), ncycles, cp, band, hist);
+    prof_end(K_PRE, st, 0.0, 0.0);
+    MSG_CHECK_LAUNCH();
+    // the host tables above are read by the copies: finish before they go out of scope
+    MSG_CUDA_TRY(cudaStreamSynchronize(st));
+    return MSG_OK;
 }

@@ -29,7 +29,9 @@ EXPORTED = ("msg_normals", "kl_prepared_bytes", "kl_prepare", "sample_field", "m
             "mimc_differences_noalloc", "msg_device_status", "msg_last_error", "msg_version",
             "msg_launch_count",
             "msg_profile_enable", "msg_profile_read", "msg_profile_read_level",
-            "ce_padding", "ce_workspace_bytes", "ce_sample_field")
+            "ce_padding", "ce_workspace_bytes", "ce_sample_field", "msg_history_workspace_bytes",
+            "msg_cycle_history")
+MSG_HIST_MSG, MSG_HIST_STANDARD = 0, 1
 MSG_CE_NEGATIVE_EIGENVALUE = 1
 KERNEL_CLASSES = ("PRE", "POST", "LOW", "RESIDUAL", "UPDATE", "INTERP", "QOI", "COEFFS", "NORMALS", "KL", "MIMC",
                   "CE")
@@ -154,6 +156,10 @@ def load(path: str | None = None):
     L.ce_workspace_bytes.restype = sz
     L.ce_sample_field.argtypes = [i32, i32, i64, ctypes.POINTER(msg_ce_law), u64, u64, vp, vp, vp, vp, sz, vp]
     L.ce_sample_field.restype = i32
+    L.msg_history_workspace_bytes.argtypes = [i32, i32, i64, ctypes.POINTER(msg_params), i32]
+    L.msg_history_workspace_bytes.restype = sz
+    L.msg_cycle_history.argtypes = [i32, i32, i64, ctypes.POINTER(msg_params), i32, vp, i32, vp, vp, sz, vp]
+    L.msg_cycle_history.restype = i32
     _lib = L
     return L
 
@@ -228,6 +234,29 @@ def ce_sample_field(P: int, Q: int, S: int, law: CeLaw, seed: int, s0: int, Z, e
         workspace = torch.empty(ce_workspace_bytes(P, Q, law), dtype=torch.uint8, device=Z.device)
     _check(load().ce_sample_field(P, Q, S, ctypes.byref(c), seed, s0, _ptr(Z), _ptr(eta_theta), _ptr(status),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def msg_history_workspace_bytes(P: int, Q: int, S: int, prm: SolverParams, method: int) -> int:
+    c = prm.c()
+    return int(load().msg_history_workspace_bytes(P, Q, S, ctypes.byref(c), method))
+
+
+def msg_cycle_history(P: int, Q: int, S: int, prm: SolverParams, method: int, Z, ncycles: int, hist=None,
+                      workspace=None, stream=None):
+    """Residual history [S][ncycles + 1] of plain cycles from u = 0 (FP64): method
+    MSG_HIST_MSG or MSG_HIST_STANDARD.  Returns the device tensor hist."""
+    import torch
+
+    c = prm.c()
+    if hist is None:
+        hist = torch.empty((S, ncycles + 1), dtype=torch.float64, device=Z.device)
+    if workspace is None:
+        workspace = torch.empty(msg_history_workspace_bytes(P, Q, S, prm, method), dtype=torch.uint8,
+                                device=Z.device)
+    _check(load().msg_cycle_history(P, Q, S, ctypes.byref(c), method, _ptr(Z), ncycles, _ptr(hist),
+                                    _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)))
+    return hist
 
 
 def msg_workspace_bytes(PQ, prm: SolverParams) -> int:

@@ -166,3 +166,18 @@ def test_circulant_embedding_host_logic(lib):
     assert lib.ce_sample_field(P, Q, 0, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_OK
     assert lib.ce_sample_field(P, Q, 2, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_ERR_INVALID
     assert lib.ce_sample_field(P, Q, -1, ctypes.byref(c), 1, 0, None, None, None, None, 0, None) == msg.MSG_ERR_INVALID
+
+
+def test_cycle_history_host_logic(lib):
+    """Workspace size and host-side checks of the convergence-study entry point."""
+    prm = msg.SolverParams()
+    a = msg.msg_history_workspace_bytes(4, 3, 5, prm, msg.MSG_HIST_MSG)
+    b = msg.msg_history_workspace_bytes(4, 3, 5, prm, msg.MSG_HIST_STANDARD)
+    assert a > 5 * 5 * 8 * (2 ** 5 - 2 + 4) * (2 ** 4 - 2 + 3) and b > 0
+    assert msg.msg_history_workspace_bytes(4, 3, 10, prm, msg.MSG_HIST_MSG) > a
+    assert msg.msg_history_workspace_bytes(4, 3, 5, prm, 2) == 0 and lib.msg_last_error() != b""
+    assert msg.msg_history_workspace_bytes(11, 3, 5, prm, 0) == 0
+    c = prm.c()
+    assert lib.msg_cycle_history(4, 3, 0, ctypes.byref(c), 0, None, 10, None, None, 0, None) == msg.MSG_OK
+    assert lib.msg_cycle_history(4, 3, 2, ctypes.byref(c), 0, None, 10, None, None, 0, None) == msg.MSG_ERR_INVALID
+    assert lib.msg_cycle_history(4, 3, 2, ctypes.byref(c), 0, None, 0, None, None, 0, None) == msg.MSG_ERR_INVALID
