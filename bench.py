@@ -64,7 +64,7 @@ def parse():
                     help="also time one step of S samples through the batched path with FP64 cycles "
                          "(separates the batching gain from the precision gain; 0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass (at most --steps)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving", "ce", "estimator"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "kl", "uneven", "serving", "ce", "estimator", "convergence"],
                     help="solve: the batched FMSG solve (default line); kl: KL field sampling at 1024^2 points, "
                          "M = 400, 8192 samples, every GEMM mode; uneven: 16 384 samples over grids 4..512 per "
                          "side in one call; serving: adaptive MIMC driver requests through continuous batching")
@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--ce-solve-S", type=int, default=256, help="ce workload: samples also solved")
     ap.add_argument("--ce-L", type=int, default=9, help="ce workload: periodic domain side (domain lengths)")
     ap.add_argument("--est-S", type=int, default=1024, help="estimator workload: samples at the top index")
+    ap.add_argument("--conv-S", type=int, default=64, help="convergence workload: samples per configuration")
+    ap.add_argument("--conv-cycles", type=int, default=30, help="convergence workload: cycles from u = 0")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -765,6 +767,58 @@ def estimator_workload(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- convergence workload --
+
+def convergence_workload(a):
+    """The convergence study of Sec. 2 on the paper's field law with fixed
+    hyper-parameters (Matern nu = 1/2, lambda = 1/4, anisotropic ratio 1/16,
+    rotation 0, 10, 20, 30 degrees, circulant-embedding fields): averaged
+    convergence factor of W(nu, nu) cycles, nu = 2..5, for MSG and for multigrid
+    with standard coarsening on square grids of 2^k cells a side, from u = 0.
+    A sample's factor is (r_m / r_0)^(1/m) with m the first cycle whose relative
+    residual is below 1e-10 (or the last cycle); a configuration where some sample
+    ends above its starting residual is reported as not converged (null)."""
+    import torch
+
+    from paper_1907_12334_gb300 import build, msg
+
+    build.build()
+    msg.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    S, n = a.conv_S, a.conv_cycles
+    ks = list(range(3, a.P + 1))
+    out = {}
+    t0 = time.perf_counter()
+    for th in (0.0, 10.0, 20.0, 30.0):
+        law = msg.CeLaw(eta_lo=1 / 16, eta_hi=1 / 16, theta_lo=th, theta_hi=th, L=a.ce_L, batch=8)
+        for k in ks:
+            Z = torch.empty((S, msg.field_points(k, k)), dtype=torch.float64, device=dev)
+            msg.ce_sample_field(k, k, S, law, 2019, 0, Z)
+            for nu in (2, 3, 4, 5):
+                prm = msg.SolverParams(nu1=nu, nu2=nu)
+                for method, name in ((msg.MSG_HIST_MSG, "MSG"), (msg.MSG_HIST_STANDARD, "MG")):
+                    h = msg.msg_cycle_history(k, k, S, prm, method, Z.reshape(-1), n).cpu().numpy()
+                    rho = []
+                    bad = False
+                    for s in range(S):
+                        below = np.nonzero(h[s] < 1e-10)[0]
+                        m = int(below[0]) if below.size else n
+                        bad |= not np.isfinite(h[s, m]) or h[s, m] >= h[s, 0]
+                        rho.append((h[s, m] / h[s, 0]) ** (1.0 / m))
+                    key = f"theta={th:g} {name} W({nu},{nu})"
+                    out.setdefault(key, {})[f"{(1 << k) - 1}x{(1 << k) - 1}"] = None if bad else float(np.mean(rho))
+    t = time.perf_counter() - t0
+    line = {"metric": "averaged convergence factor (MSG vs standard coarsening)", "value": None, "unit": "factor",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Sec. 2 convergence study: Matern nu=1/2, lambda=1/4, eta=1/16, theta in "
+                                   f"{{0,10,20,30}} deg (circulant embedding, L={a.ce_L}), {S} samples, {n} cycles "
+                                   f"from u=0, grids {(1 << ks[0]) - 1}^2..{(1 << ks[-1]) - 1}^2 unknowns",
+                       "S": S, "cycles": n},
+            "seconds": t, "factors": out}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ uneven workload --
 
 def uneven_workload(a):
@@ -976,10 +1030,11 @@ def main():
     if a.impl == "reference":
         reference_arm(a, rank, world)
         return
-    if a.workload in ("kl", "uneven", "serving", "ce", "estimator"):
+    if a.workload in ("kl", "uneven", "serving", "ce", "estimator", "convergence"):
         if rank == 0:
             {"kl": kl_workload, "uneven": uneven_workload, "serving": serving_workload,
-             "ce": ce_workload, "estimator": estimator_workload}[a.workload](a)
+             "ce": ce_workload, "estimator": estimator_workload,
+             "convergence": convergence_workload}[a.workload](a)
         return
     if world > 1:
         import torch
