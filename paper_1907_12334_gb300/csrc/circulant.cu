@@ -69,6 +69,22 @@ __global__ void k_ce_hyper(uint64_t seed, uint64_t s0, int n, CeLawDev law, doub
 // Generating array of sample blockIdx.y: c[k2][k1] = C(d1 hx, d2 hy) with d
 // the signed periodic offset (k, or k - M above M/2); at k = M/2 both signs
 // are averaged so that the embedding stays symmetric under the rotation.
+// C(-d) = C(d) bit for bit (the rotated offset only changes sign), so half of
+// the points are evaluated and each value is also stored at its mirror
+// (-k1, -k2) mod (M1, M2): the rows 1..M2/2-1 whole, and the first half of
+// the two rows that are their own mirror (k2 = 0 and k2 = M2/2).
+__device__ __forceinline__ double ce_cov_at(int k1, int k2, int M1, int M2, double hx, double hy, double ct,
+                                            double st, double ieta_lam, double ilam, double nu)
+{
+    const int d1 = k1 <= M1 / 2 ? k1 : k1 - M1, d2 = k2 <= M2 / 2 ? k2 : k2 - M2;
+    const double dx = d1 * hx, dy = d2 * hy;
+    if (2 * k1 != M1 && 2 * k2 != M2) return ce_cov(dx, dy, ct, st, ieta_lam, ilam, nu);
+    const double dx2 = (2 * k1 == M1) ? -dx : dx, dy2 = (2 * k2 == M2) ? -dy : dy;
+    return (ce_cov(dx, dy, ct, st, ieta_lam, ilam, nu) + ce_cov(dx, dy2, ct, st, ieta_lam, ilam, nu) +
+            ce_cov(dx2, dy, ct, st, ieta_lam, ilam, nu) + ce_cov(dx2, dy2, ct, st, ieta_lam, ilam, nu)) /
+           4.0;
+}
+
 __global__ void k_ce_cov(int M1, int M2, double hx, double hy, CeLawDev law, const double* et, double* c)
 {
     const int64_t N = (int64_t)M1 * M2;
@@ -76,20 +92,22 @@ __global__ void k_ce_cov(int M1, int M2, double hx, double hy, CeLawDev law, con
     const double eta = et[2 * b], th = et[2 * b + 1];
     const double ct = cos(th), st = sin(th), ieta_lam = 1.0 / (eta * law.lam), ilam = 1.0 / law.lam;
     double* cb = c + (int64_t)b * N;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        const int k2 = (int)(k / M1), k1 = (int)(k - (int64_t)k2 * M1);
-        const int d1 = k1 <= M1 / 2 ? k1 : k1 - M1, d2 = k2 <= M2 / 2 ? k2 : k2 - M2;
-        const double dx = d1 * hx, dy = d2 * hy;
-        double v;
-        if (2 * k1 != M1 && 2 * k2 != M2) {
-            v = ce_cov(dx, dy, ct, st, ieta_lam, ilam, law.nu);
-        } else {  // half-period offset: average over both signs of that coordinate
-            const double dx2 = (2 * k1 == M1) ? -dx : dx, dy2 = (2 * k2 == M2) ? -dy : dy;
-            v = (ce_cov(dx, dy, ct, st, ieta_lam, ilam, law.nu) + ce_cov(dx, dy2, ct, st, ieta_lam, ilam, law.nu) +
-                 ce_cov(dx2, dy, ct, st, ieta_lam, ilam, law.nu) + ce_cov(dx2, dy2, ct, st, ieta_lam, ilam, law.nu)) /
-                4.0;
+    const int64_t full = (int64_t)(M2 / 2 - 1) * M1, self = 2 * (int64_t)(M1 / 2 + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < full + self;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k1, k2;
+        if (t < full) {
+            k2 = 1 + (int)(t / M1);
+            k1 = (int)(t - (int64_t)(k2 - 1) * M1);
+        } else {
+            const int64_t u = t - full;
+            k2 = u < M1 / 2 + 1 ? 0 : M2 / 2;
+            k1 = (int)(u < M1 / 2 + 1 ? u : u - (M1 / 2 + 1));
         }
-        cb[k] = v;
+        const double v = ce_cov_at(k1, k2, M1, M2, hx, hy, ct, st, ieta_lam, ilam, law.nu);
+        const int m1 = (M1 - k1) % M1, m2 = (M2 - k2) % M2;
+        cb[(int64_t)k2 * M1 + k1] = v;
+        cb[(int64_t)m2 * M1 + m1] = v;
     }
 }
 
@@ -128,7 +146,7 @@ __global__ void k_ce_scale(int M1, int M2, uint64_t seed, uint64_t s0, const dou
             const int k2 = (int)(k / M1), k1 = (int)(k - (int64_t)k2 * M1);
             const double lam = ce_lambda(sp, M1, M2, k1, k2);
             neg |= lam < -1e-10 * l0;
-            const float a = (float)sqrt(fmax(lam, 0.0) * inv_n);
+            const float a = sqrtf((float)(fmax(lam, 0.0) * inv_n));  // single precision suffices: a is a float
             const double ua = (double)(w[2 * h] >> 11) * inv53, ub = (double)(w[2 * h + 1] >> 11) * inv53;
             const float lg = ua < 0.5 ? log1pf(-(float)ua) : logf((float)(1.0 - ua));
             const float rad = a * sqrtf(-2.0f * lg);
@@ -294,7 +312,7 @@ extern "C" int32_t ce_sample_field(int32_t P, int32_t Q, int64_t S, const msg_ce
         MSG_CHECK_LAUNCH();
         prof_begin(K_CE, st);
         k_ce_cov<<<dim3(gx, nb), 256, 0, st>>>(z.M1, z.M2, hx, hy, ld, et, c);
-        prof_end(K_CE, st, 8.0 * z.N * nb, 40.0 * z.N * nb);
+        prof_end(K_CE, st, 8.0 * z.N * nb, 20.0 * z.N * nb);
         MSG_CHECK_LAUNCH();
         {
             std::lock_guard<std::mutex> lk(g_plan_mu);
