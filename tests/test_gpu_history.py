@@ -60,5 +60,5 @@ def test_history_shows_the_anisotropy_effect(msg):
     Z = torch.zeros(S * oracle.field_points(P, Q), dtype=torch.float64, device=DEV)
     hs = msg.msg_cycle_history(P, Q, S, msg.SolverParams(), 1, Z, n).cpu().numpy()
     hm = msg.msg_cycle_history(P, Q, S, msg.SolverParams(), 0, Z, n).cpu().numpy()
-    assert (hs[:, n] / hs[:, 0]) ** (1 / n) > 0.4
-    assert (hm[:, 6] / hm[:, 0]) ** (1 / 6) < 0.1
+    assert ((hs[:, n] / hs[:, 0]) ** (1 / n) > 0.4).all()
+    assert ((hm[:, 6] / hm[:, 0]) ** (1 / 6) < 0.1).all()
