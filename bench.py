@@ -775,7 +775,8 @@ def convergence_workload(a):
     rotation 0, 10, 20, 30 degrees, circulant-embedding fields): averaged
     convergence factor of W(nu, nu) cycles, nu = 2..5, for MSG and for multigrid
     with standard coarsening on square grids of 2^k cells a side, from u = 0.
-    A sample's factor is (r_m / r_0)^(1/m) with m the first cycle whose relative
+    Both readings of the distance's scaling S (printed, and lambda as a length) are
+    run.  A sample's factor is (r_m / r_0)^(1/m) with m the first cycle whose relative
     residual is below 1e-10 (or the last cycle); a configuration where some sample
     ends above its starting residual is reported as not converged (null)."""
     import torch
@@ -790,8 +791,8 @@ def convergence_workload(a):
     ks = list(range(3, a.P + 1))
     out = {}
     t0 = time.perf_counter()
-    for th in (0.0, 10.0, 20.0, 30.0):
-        law = msg.CeLaw(eta_lo=1 / 16, eta_hi=1 / 16, theta_lo=th, theta_hi=th, L=a.ce_L, batch=8)
+    for scale, th in [(sc, t) for sc in (0, 1) for t in (0.0, 10.0, 20.0, 30.0)]:
+        law = msg.CeLaw(eta_lo=1 / 16, eta_hi=1 / 16, theta_lo=th, theta_hi=th, L=a.ce_L, batch=8, scale=scale)
         for k in ks:
             Z = torch.empty((S, msg.field_points(k, k)), dtype=torch.float64, device=dev)
             msg.ce_sample_field(k, k, S, law, 2019, 0, Z)
@@ -806,7 +807,7 @@ def convergence_workload(a):
                         m = int(below[0]) if below.size else n
                         bad |= not np.isfinite(h[s, m]) or h[s, m] >= h[s, 0]
                         rho.append((h[s, m] / h[s, 0]) ** (1.0 / m))
-                    key = f"theta={th:g} {name} W({nu},{nu})"
+                    key = f"{'S printed' if scale == 0 else 'lambda a length'} theta={th:g} {name} W({nu},{nu})"
                     out.setdefault(key, {})[f"{(1 << k) - 1}x{(1 << k) - 1}"] = None if bad else float(np.mean(rho))
     t = time.perf_counter() - t0
     line = {"metric": "averaged convergence factor (MSG vs standard coarsening)", "value": None, "unit": "factor",

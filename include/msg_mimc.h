@@ -157,6 +157,10 @@ typedef struct {
     double theta_lo, theta_hi; /* rotation range, degrees */
     int32_t L;                 /* periodic domain side in domain lengths (ce_padding: Sec. 4's choice) */
     int32_t batch;             /* samples per FFT batch: the workspace grows with it */
+    int32_t scale;             /* 0: r = ||S R dx|| with S = diag(1/sqrt(eta lambda), 1/sqrt(lambda)) as
+                                  Sec. 1 prints it; 1: lambda read as a length, S = diag(1/(eta lambda),
+                                  1/lambda) (the reading under which standard coarsening fails as Sec. 2
+                                  reports) */
 } msg_ce_law;
 #define MSG_CE_NEGATIVE_EIGENVALUE 1
 /* L = 1 + 2 ceil(sqrt(nu) log2(max(2^p0, 2^q0))) (Sec. 4); 0 on bad input. */

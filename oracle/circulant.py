@@ -23,6 +23,11 @@ Readings (where the text leaves a choice):
   forward transform (exp(-2 pi i jk/M)), restricted to the field's nodes;
   xi1, xi2 at embedding point k = k2 M1 + k1 are normals 2k and 2k+1 of the
   sample's Philox4x64-10 + Box-Muller stream;
+* the scaling S: the text prints S = diag(1/sqrt(eta lambda), 1/sqrt(lambda))
+  (scale 0, the default), under which lambda acts as a squared length; with
+  lambda read as a length, S = diag(1/(eta lambda), 1/lambda) (scale 1), the
+  standard-coarsening multigrid of Sec. 2 fails at eta = 1/16 as the paper
+  reports, while under the printed form it converges;
 * eta and theta of global sample s come from one Philox4x64-10 block with
   counter (0, s, 1, 0) and key (seed, 0): u = (w >> 11) 2^-53 of words 0 and
   1, eta = eta_lo + (eta_hi - eta_lo) u0, theta = theta_lo + (theta_hi -
@@ -48,6 +53,7 @@ class CeLaw:
     theta_lo: float = -30.0  # degrees
     theta_hi: float = 30.0
     L: int = 7               # periodic domain side in domain lengths
+    scale: int = 0           # 0: S = diag(1/sqrt(eta lam), 1/sqrt(lam)) as printed; 1: lambda as a length
 
 
 def padding(nu: float, p0: int, q0: int) -> int:
@@ -69,11 +75,14 @@ def matern(r, nu: float):
     raise ValueError("nu must be 1/2, 3/2 or 5/2")
 
 
-def distance(dx, dy, lam: float, eta: float, theta: float):
-    """r = ||S R (dx, dy)||, theta in radians (Sec. 1)."""
+def distance(dx, dy, lam: float, eta: float, theta: float, scale: int = 0):
+    """r = ||S R (dx, dy)||, theta in radians (Sec. 1).  scale 0: S = diag(1/sqrt(eta
+    lambda), 1/sqrt(lambda)) as printed; 1: S = diag(1/(eta lambda), 1/lambda)."""
     ct, st = math.cos(theta), math.sin(theta)
     rx = ct * dx - st * dy
     ry = st * dx + ct * dy
+    if scale:
+        return np.sqrt((rx / (eta * lam)) ** 2 + (ry / lam) ** 2)
     return np.sqrt(rx * rx / (eta * lam) + ry * ry / lam)
 
 
@@ -109,7 +118,7 @@ def generating_array(P: int, Q: int, law: CeLaw, eta: float, theta: float) -> np
     c = np.zeros((M2, M1))
     for ox in (a1, b1):
         for oy in (a2, b2):
-            c += matern(distance(ox[None, :] * hx, oy[:, None] * hy, law.lam, eta, theta), law.nu)
+            c += matern(distance(ox[None, :] * hx, oy[:, None] * hy, law.lam, eta, theta, law.scale), law.nu)
     return c / 4.0
 
 
@@ -140,4 +149,5 @@ def covariance_matrix(P: int, Q: int, law: CeLaw, eta: float, theta: float) -> n
     nx, ny = (1 << (P + 1)) + 1, (1 << (Q + 1)) + 1
     X, Y = np.meshgrid(np.arange(nx) * 2.0 ** -(P + 1), np.arange(ny) * 2.0 ** -(Q + 1))
     X, Y = X.ravel(), Y.ravel()
-    return matern(distance(X[:, None] - X[None, :], Y[:, None] - Y[None, :], law.lam, eta, theta), law.nu)
+    return matern(distance(X[:, None] - X[None, :], Y[:, None] - Y[None, :], law.lam, eta, theta, law.scale),
+                  law.nu)

@@ -31,6 +31,7 @@ namespace {
 
 struct CeLawDev {
     double nu, lam, eta_lo, eta_hi, th_lo, th_hi;  // rotation range in degrees
+    int scale;                                     // 0: S as Sec. 1 prints it; 1: lambda as a length
 };
 
 // Eq. (1.2) for half-integer smoothness, x = 2 sqrt(nu) r:
@@ -90,7 +91,10 @@ __global__ void k_ce_cov(int M1, int M2, double hx, double hy, CeLawDev law, con
     const int64_t N = (int64_t)M1 * M2;
     const int b = blockIdx.y;
     const double eta = et[2 * b], th = et[2 * b + 1];
-    const double ct = cos(th), st = sin(th), ieta_lam = 1.0 / (eta * law.lam), ilam = 1.0 / law.lam;
+    const double ct = cos(th), st = sin(th);
+    // r^2 = rx^2 ieta_lam + ry^2 ilam: S = diag(1/sqrt(eta lam), 1/sqrt(lam)) or diag(1/(eta lam), 1/lam)
+    const double ieta_lam = law.scale ? 1.0 / ((eta * law.lam) * (eta * law.lam)) : 1.0 / (eta * law.lam);
+    const double ilam = law.scale ? 1.0 / (law.lam * law.lam) : 1.0 / law.lam;
     double* cb = c + (int64_t)b * N;
     const int64_t full = (int64_t)(M2 / 2 - 1) * M1, self = 2 * (int64_t)(M1 / 2 + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < full + self;
@@ -244,6 +248,7 @@ int ce_validate(int P, int Q, const msg_ce_law* law)
         return MSG_ERR_INVALID;
     }
     // L >= 2: the periodic grid must hold every field node (2^(P+1) + 1 of them a row)
+    if (law->scale != 0 && law->scale != 1) { set_error("law: scale must be 0 or 1"); return MSG_ERR_INVALID; }
     if (law->L < 2 || law->L > 64 || law->batch < 1) { set_error("law: need 2 <= L <= 64, batch >= 1"); return MSG_ERR_INVALID; }
     return MSG_OK;
 }
@@ -293,7 +298,7 @@ extern "C" int32_t ce_sample_field(int32_t P, int32_t Q, int64_t S, const msg_ce
     double* c = (double*)(ws + z.et);                // generating arrays (FP64) ...
     float2* smp = (float2*)(ws + z.et);              // ... then, in the same bytes, the sample spectra
     double2* spec = (double2*)(ws + z.et + z.buf);   // eigenvalues (half spectra)
-    const CeLawDev ld{law->nu, law->lambda, law->eta_lo, law->eta_hi, law->theta_lo, law->theta_hi};
+    const CeLawDev ld{law->nu, law->lambda, law->eta_lo, law->eta_hi, law->theta_lo, law->theta_hi, law->scale};
     const double hx = std::ldexp(1.0, -(P + 1)), hy = std::ldexp(1.0, -(Q + 1));
     const int64_t nf = (int64_t)z.nfx * z.nfy;
     if (status) MSG_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t) * S, st));

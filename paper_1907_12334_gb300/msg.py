@@ -77,7 +77,7 @@ class SolverParams:
 class msg_ce_law(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("lam", ctypes.c_double), ("eta_lo", ctypes.c_double),
                 ("eta_hi", ctypes.c_double), ("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
-                ("L", ctypes.c_int32), ("batch", ctypes.c_int32)]
+                ("L", ctypes.c_int32), ("batch", ctypes.c_int32), ("scale", ctypes.c_int32)]
 
 
 @dataclass
@@ -92,10 +92,11 @@ class CeLaw:
     theta_hi: float = 30.0
     L: int = 7
     batch: int = 8
+    scale: int = 0  # 0: S as Sec. 1 prints it; 1: lambda as a length (see msg_mimc.h)
 
     def c(self) -> msg_ce_law:
         return msg_ce_law(self.nu, self.lam, self.eta_lo, self.eta_hi, self.theta_lo, self.theta_hi, self.L,
-                          self.batch)
+                          self.batch, self.scale)
 
 
 _lib = None

@@ -37,10 +37,11 @@ def _field_covariance(P, Q, law, eta, theta):
     return A @ A.T, lam
 
 
-@pytest.mark.parametrize("P,Q,nu,eta,theta_deg", [(1, 1, 0.5, 0.125, 20.0), (1, 2, 0.5, 1 / 16, -30.0),
-                                                  (2, 1, 1.5, 0.25, 25.0), (1, 1, 2.5, 0.2, 0.0)])
-def test_embedding_reproduces_the_matern_covariance_exactly(P, Q, nu, eta, theta_deg):
-    law = ce.CeLaw(nu=nu, L=7)
+@pytest.mark.parametrize("P,Q,nu,eta,theta_deg,scale", [(1, 1, 0.5, 0.125, 20.0, 0), (1, 2, 0.5, 1 / 16, -30.0, 0),
+                                                        (2, 1, 1.5, 0.25, 25.0, 0), (1, 1, 2.5, 0.2, 0.0, 0),
+                                                        (1, 2, 0.5, 1 / 16, 10.0, 1), (2, 1, 1.5, 0.1, -20.0, 1)])
+def test_embedding_reproduces_the_matern_covariance_exactly(P, Q, nu, eta, theta_deg, scale):
+    law = ce.CeLaw(nu=nu, L=7, scale=scale)
     th = math.radians(theta_deg)
     cov, lam = _field_covariance(P, Q, law, eta, th)
     assert lam.min() >= -1e-12 * lam.max()
@@ -67,6 +68,13 @@ def test_distance_at_special_angles():
     # +30 degrees moves (cos 30, sin 30) onto the first axis only for theta = -30 degrees
     v = (math.cos(math.radians(30)), math.sin(math.radians(30)))
     assert ce.distance(*v, lam, eta, math.radians(-30)) == pytest.approx(1 / math.sqrt(eta * lam), rel=1e-14)
+
+
+def test_distance_length_scale_reading():
+    """scale 1 reads lambda as a length: r = |rotated offset| / (eta lambda) along x'."""
+    lam, eta, dx = 0.25, 0.1, 0.3
+    assert ce.distance(dx, 0.0, lam, eta, 0.0, 1) == pytest.approx(dx / (eta * lam), rel=1e-15)
+    assert ce.distance(0.0, dx, lam, eta, math.pi / 2, 1) == pytest.approx(dx / (eta * lam), rel=1e-14)
 
 
 def test_padding_formula():

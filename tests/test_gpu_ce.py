@@ -63,7 +63,7 @@ def _run(msg, P, Q, S, law_kw, seed, s0, batch):
 
 
 @pytest.mark.parametrize("P,Q,S,batch,law_kw", [(3, 3, 5, 2, {}), (2, 4, 3, 3, {}), (4, 1, 4, 4, dict(nu=1.5)),
-                                                (1, 1, 2, 1, dict(nu=2.5, lam=0.1, L=5))])
+                                                (1, 1, 2, 1, dict(nu=2.5, lam=0.1, L=5)), (3, 4, 3, 2, dict(scale=1))])
 def test_ce_fields_match_oracle(msg, P, Q, S, batch, law_kw):
     """Ragged last batch (S not a multiple of batch), anisotropic grids, the three
     smoothness values, a smaller padding."""
