@@ -148,6 +148,25 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp64_dgemm_tflops(dev, n=8192, reps=3):
+    """FP64 reference rate of this GPU: a cuBLAS DGEMM n^3 (through torch), CUDA events.
+    GB300's FP64 rate is far below its FP32 one; this is the denominator the FP64
+    paths are compared with."""
+    import torch
+
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn_like(a)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(a, b)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return reps * 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1000.0) / 1e12
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -398,7 +417,8 @@ def ours(a, rank, world, local_rank):
         c64 = int((st64.cpu().numpy() == 0).sum())
         del ws64
         batched64 = {"value": c64 / t, "unit": "samples/s", "samples": S64, "converged": c64,
-                     "batched_mixed_over_batched_fp64": value / (c64 / t) if c64 else None}
+                     "batched_mixed_over_batched_fp64": value / (c64 / t) if c64 else None,
+                     "fp64_dgemm_tflops_measured": fp64_dgemm_tflops(dev)}
 
     # ---- optional: one untimed step with every launch timed, per multigrid diagonal
     if a.profile_levels and rank == 0:
