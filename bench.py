@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--ce-batch", type=int, default=16, help="ce workload: samples per FFT batch")
     ap.add_argument("--ce-solve-S", type=int, default=256, help="ce workload: samples also solved")
     ap.add_argument("--ce-L", type=int, default=9, help="ce workload: periodic domain side (domain lengths)")
+    ap.add_argument("--ce-scale", type=int, default=0, choices=[0, 1],
+                    help="ce/estimator workloads: distance scaling (0: as printed, 1: lambda as a length)")
     ap.add_argument("--est-S", type=int, default=1024, help="estimator workload: samples at the top index")
     ap.add_argument("--conv-S", type=int, default=64, help="convergence workload: samples per configuration")
     ap.add_argument("--conv-cycles", type=int, default=30, help="convergence workload: cycles from u = 0")
@@ -636,7 +638,7 @@ def ce_workload(a):
     # Sec. 4's padding with p0 = q0 = 4 is L = 7; at the 1/512 field spacing that leaves
     # eigenvalues down to -2e-7 of the largest, and L = 9 removes them (the default here)
     L = a.ce_L
-    law = msg.CeLaw(L=L, batch=B)
+    law = msg.CeLaw(L=L, batch=B, scale=a.ce_scale)
     nf = msg.field_points(P, Q)
     M1, M2 = L << (P + 1), L << (Q + 1)
     N, H = M1 * M2, M2 * (M1 // 2 + 1)
@@ -662,7 +664,7 @@ def ce_workload(a):
     ours = msg.msg_profile_read("CE")
     msg.msg_profile_enable(False)
     neg = int((st != 0).sum())
-    Zo, eta, theta, ratio = oce.ce_field(P, Q, oce.CeLaw(L=L), seed, 0)
+    Zo, eta, theta, ratio = oce.ce_field(P, Q, oce.CeLaw(L=L, scale=a.ce_scale), seed, 0)
     err = float(np.max(np.abs(Z[0].cpu().numpy() - Zo)))
     # algorithmic bytes of one sample: c written and read by D2Z (8N each), its half
     # spectrum written and read (16H each), the scaled spectrum written and read by C2C
@@ -731,7 +733,7 @@ def estimator_workload(a):
     K = a.P - p0
     P = Q = a.P
     S, seed = a.est_S, 1907
-    law = msg.CeLaw(L=a.ce_L, batch=min(16, S))
+    law = msg.CeLaw(L=a.ce_L, batch=min(16, S), scale=a.ce_scale)
     nf = msg.field_points(P, Q)
     Z = torch.empty((S, nf), dtype=torch.float64, device=dev)
     st = torch.empty(S, dtype=torch.int32, device=dev)
@@ -780,7 +782,8 @@ def estimator_workload(a):
     line = {"metric": "MSG-MIMC sample-reuse cost ratio (Theorem 1)", "value": out["Q3"]["allocation_ratio_measured_V_C"],
             "unit": "cost with reuse / without", "n_gpus": 1, "higher_is_better": False,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"paper's field law (Sec. 4, circulant embedding L={a.ce_L}), S={S} samples at "
+            "config": {"workload": f"paper's field law (Sec. 4, circulant embedding L={a.ce_L}, distance scaling "
+                                   f"{'as printed' if a.ce_scale == 0 else 'lambda as a length'}), S={S} samples at "
                                    f"the top index L=({K},{K}) over p0=q0={p0} (grids up to {2**P}x{2**Q}), "
                                    f"Q1/Q2/Q3, eps={a.eps}", "S": S, "K": K, "p0": p0},
             "seconds": {"sampling": t_ce, "solves": t_solve}, "qoi": out}
