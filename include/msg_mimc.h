@@ -148,8 +148,9 @@ int32_t sample_field(const void* prepared, int64_t npts, int32_t M, int32_t mode
 /*             aligned.  1 <= P, Q <= 10, S >= 0, nu in {0.5, 1.5, 2.5},      */
 /*             lambda > 0, 0 < eta_lo <= eta_hi, 2 <= L <= 64 (the periodic  */
 /*             grid holds every field node), batch >= 1.                     */
-/* Asynchronous on `stream`; the first call for a (P, Q, L, batch) creates   */
-/* and caches the cuFFT plans (which allocate device memory and block).      */
+/* Asynchronous on `stream`; the first call for a (P, Q, L, batch) on a      */
+/* stream creates and caches that stream's cuFFT plans (which allocate their */
+/* own work areas and block); plans are never shared between streams.        */
 typedef struct {
     double nu;                 /* Matern smoothness: 0.5, 1.5 or 2.5 (closed forms of Eq. (1.2)) */
     double lambda;             /* length scale */

@@ -198,17 +198,19 @@ CeSizes ce_sizes(int P, int Q, const msg_ce_law& law)
     return z;
 }
 
-// cuFFT plans, created on first use for a (device, M1, M2, batch, kind) and
-// kept for the life of the library; exec calls are serialised with their
-// cufftSetStream under the same lock.
+// cuFFT plans, created on first use for a (device, stream, M1, M2, batch,
+// kind) and kept for the life of the library.  A plan owns its work area, so
+// plans are not shared between streams: transforms on two streams never run
+// in one work area at once, and on one stream they are ordered by the stream.
+// The map and cufftSetStream + exec are guarded by one lock.
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int, int, int>, cufftHandle> g_plans;
+std::map<std::tuple<int, uintptr_t, int, int, int, int>, cufftHandle> g_plans;
 
-int ce_plan(int M1, int M2, int batch, bool d2z, cufftHandle* out)
+int ce_plan(cudaStream_t st, int M1, int M2, int batch, bool d2z, cufftHandle* out)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, M1, M2, batch, d2z ? 1 : 0);
+    const auto key = std::make_tuple(dev, (uintptr_t)st, M1, M2, batch, d2z ? 1 : 0);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {
         *out = it->second;
@@ -322,8 +324,8 @@ extern "C" int32_t ce_sample_field(int32_t P, int32_t Q, int64_t S, const msg_ce
         {
             std::lock_guard<std::mutex> lk(g_plan_mu);
             cufftHandle pd, pc;
-            if ((rc = ce_plan(z.M1, z.M2, nb, true, &pd)) != MSG_OK) return rc;
-            if ((rc = ce_plan(z.M1, z.M2, nb, false, &pc)) != MSG_OK) return rc;
+            if ((rc = ce_plan(st, z.M1, z.M2, nb, true, &pd)) != MSG_OK) return rc;
+            if ((rc = ce_plan(st, z.M1, z.M2, nb, false, &pc)) != MSG_OK) return rc;
             if (cufftSetStream(pd, st) != CUFFT_SUCCESS ||
                 cufftExecD2Z(pd, (cufftDoubleReal*)c, (cufftDoubleComplex*)spec) != CUFFT_SUCCESS) {
                 set_error("cuFFT D2Z failed");
