@@ -78,8 +78,9 @@ def parse():
     ap.add_argument("--ce-scale", type=int, default=0, choices=[0, 1],
                     help="ce/estimator workloads: distance scaling (0: as printed, 1: lambda as a length)")
     ap.add_argument("--est-S", type=int, default=1024, help="estimator workload: samples at the top index")
-    ap.add_argument("--conv-S", type=int, default=64, help="convergence workload: samples per configuration")
-    ap.add_argument("--conv-cycles", type=int, default=30, help="convergence workload: cycles from u = 0")
+    ap.add_argument("--conv-S", type=int, default=32, help="convergence workload: samples per configuration")
+    ap.add_argument("--conv-cycles", type=int, default=20, help="convergence workload: cycles from u = 0")
+    ap.add_argument("--conv-kmax", type=int, default=7, help="convergence workload: largest grid 2^k cells a side")
     ap.add_argument("--profile-levels", default="", metavar="PATH",
                     help="after the timed region, run one more step timing every launch and write the "
                          "per-diagonal times of the multigrid kernel classes to PATH (JSON)")
@@ -811,7 +812,7 @@ def convergence_workload(a):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     S, n = a.conv_S, a.conv_cycles
-    ks = list(range(3, a.P + 1))
+    ks = list(range(3, a.conv_kmax + 1))
     out = {}
     t0 = time.perf_counter()
     for scale, th in [(sc, t) for sc in (0, 1) for t in (0.0, 10.0, 20.0, 30.0)]:
