@@ -16,9 +16,6 @@ import itertools
 import numpy as np
 import pytest
 
-AHEAD = 4  # kStreamAhead
-
-
 def split_slot(h, i):
     return h + (i >> 1) if i & 1 else i >> 1
 
