@@ -24,3 +24,22 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_every_workload_and_option_parses():
+    """The argument parser accepts every workload and its options (CPU, no run)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    argv = sys.argv
+    try:
+        for extra in (["--workload", "kl", "--kl-n", "64", "--kl-S", "8", "--kl-chunk", "8"],
+                      ["--workload", "uneven"], ["--workload", "serving"],
+                      ["--workload", "ce", "--ce-S", "4", "--ce-batch", "2", "--ce-L", "7", "--ce-scale", "1",
+                       "--ce-solve-S", "2"],
+                      ["--workload", "estimator", "--est-S", "16"],
+                      ["--workload", "convergence", "--conv-S", "4", "--conv-cycles", "5", "--conv-kmax", "4"]):
+            sys.argv = ["bench.py"] + extra
+            assert bench.parse().workload == extra[1]
+    finally:
+        sys.argv = argv
